@@ -1,0 +1,166 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) anisotropic-equilibrium BGK lattice Boltzmann library.
+ *
+ * Method: Kruger, Weinmiller, Latz, Danner, "Lattice Boltzmann Methods with Anisotropic
+ * Equilibrium Distributions". One time step is the fully discrete BGK LBE of Eq. (LBE_BGK),
+ *     f_i(x + c_i, t + 1) = f_i(x, t) + (feq_i(x, t) - f_i(x, t)) / tau,
+ * with the third-order discrete anisotropic equilibrium of Eq. (3rd_order_equilibrium)/(feq_i):
+ *     feq_i = w_i rho [1 + u.c_i/cs2 + ((u.c_i)^2 - cs2 |u|^2 + h_i)/(2 cs2^2)
+ *                      + ((u.c_i)^3 - 3 cs2 |u|^2 u.c_i + 3 h_i u.c_i - 6 cs2 c_i.K~.u)/(6 cs2^3)],
+ *     K~ = Theta - cs2 I (Eq. K-term with Theta = cs2 A^{-1}), h_i = c_i.K~.c_i - cs2 tr K~,
+ * on the D2Q9, D3Q19 and D3Q27 velocity sets (Appendix C; cs2 = 1/3). The second moment of the
+ * equilibrium is rho (Theta + u u) (Appendix E), so Theta is the anisotropy tensor in lattice
+ * units; Theta = cs2 I is standard BGK. Walls are half-way bounce-back on a solid mask (the paper
+ * names bounce-back only as future work, Sec. 5; the textbook rule is used).
+ *
+ * Conventions for every call:
+ *   - Cells are indexed n = x + nx*(y + ny*z); D2Q9 requires nz == 1.
+ *   - Field buffers are DEVICE pointers owned by the caller, element type double when the
+ *     context stores FP64 and float otherwise. Layouts: rho [N]; u [d][N]; Pi [d(d+1)/2][N]
+ *     ordered xx, yy, (zz), xy, (xz, yz). The velocity u is the paper's lattice velocity s.
+ *   - Theta is a HOST array of d*d doubles, row-major, symmetric positive definite.
+ *   - Every call is issued on the context's stream and returns without synchronising unless it
+ *     says so; an asynchronous CUDA error surfaces at the next synchronising call.
+ *   - Return value: LBM_OK (0) or a negative lbm_status. Nothing throws across this boundary.
+ *     lbm_last_error() gives a one-line description of the last failure of a context.
+ *   - The state visible to the user after lbm_init followed by lbm_step(n) is the pre-collision
+ *     population set f(n); lbm_moments and lbm_populations report it.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Velocity sets (Appendix C). */
+enum lbm_lattice { LBM_D2Q9 = 9, LBM_D3Q19 = 19, LBM_D3Q27 = 27 };
+
+/* Population storage. Arithmetic is FP32 except in LBM_FP64. Shifted forms store
+ * f_i - r_i with r_i = feq_i(rho0, u = 0; Theta) = w_i rho0 (1 + h_i/(2 cs2^2)), the rest
+ * equilibrium (equals w_i rho0 when Theta = cs2 I). */
+enum lbm_storage { LBM_FP32 = 0, LBM_FP64 = 1, LBM_FP32_SHIFTED = 2, LBM_FP16_SHIFTED = 3 };
+
+/* Streaming schemes: two arrays in pull form, or one array in the AA pattern (in place). */
+enum lbm_scheme { LBM_PULL2 = 0, LBM_AA = 1 };
+
+enum lbm_status {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = -1, /* bad pointer, size, enum or option */
+    LBM_ERR_NOT_SPD = -2,     /* Theta not symmetric positive definite */
+    LBM_ERR_BAD_TAU = -3,     /* tau <= 1/2 (non-positive viscosity, Sec. 3) */
+    LBM_ERR_OOM = -4,         /* device or host allocation failed */
+    LBM_ERR_CUDA = -5,        /* a CUDA runtime call or kernel launch failed */
+    LBM_ERR_UNSTABLE = -6,    /* a cell reached rho <= 0 or a non-finite value */
+    LBM_ERR_NO_FORWARD = -7,  /* adjoint asked for n steps but n steps were not run since init */
+    LBM_ERR_TIMEOUT = -8,     /* reserved for bounded device waits (none are used) */
+    LBM_ERR_STATE = -9        /* call out of order (e.g. step before init) */
+};
+
+/* Allocator hooks for library-owned device memory (populations, adjoint buffers, checkpoints).
+ * alloc returns a device pointer of at least `bytes` bytes, 256-byte aligned, or NULL. */
+typedef void* (*lbm_alloc_fn)(size_t bytes, void* user);
+typedef void (*lbm_free_fn)(void* ptr, void* user);
+
+typedef struct {
+    int storage;              /* enum lbm_storage; default LBM_FP32 */
+    int scheme;               /* enum lbm_scheme; default LBM_PULL2 */
+    int order;                /* 3 (default, also when 0) or 2: equilibrium truncation order */
+    double rho0;              /* reference density of the shifted forms; 0 -> 1.0 */
+    int check_every;          /* > 0: lbm_step synchronises and checks stability every k steps */
+    int use_graphs;           /* 0: CUDA graphs for small grids, 1: always, -1: never */
+    lbm_alloc_fn alloc;       /* NULL: cudaMalloc */
+    lbm_free_fn free;         /* must be set together with alloc */
+    void* alloc_user;         /* passed to alloc/free */
+    void* stream;             /* cudaStream_t for every launch; NULL: the legacy default stream */
+    size_t adjoint_mem_limit; /* bytes of device memory the adjoint may hold for saved states;
+                                 0: free device memory minus a 2 GiB margin */
+} lbm_options;
+
+/* Fill *opt with the defaults (all zero except as documented above). */
+int lbm_options_default(lbm_options* opt);
+
+/* Create a context for an nx*ny*nz lattice with relaxation time tau (Eq. LBE_BGK; kinematic
+ * viscosity (tau - 1/2) Theta, Eq. NSprefinal2) and anisotropy Theta (host, d*d).
+ * solid_mask: N bytes, nonzero = solid cell, host or device memory (detected), or NULL for an
+ * all-fluid periodic box. Boundaries are periodic on every axis; walls come only from the mask.
+ * Synchronises. On success *out owns the context; release it with lbm_destroy. */
+int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau, const double* Theta,
+               const uint8_t* solid_mask);
+int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau, const double* Theta,
+                  const uint8_t* solid_mask, const lbm_options* opt);
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Change tau or Theta of an existing context (same validation as lbm_create). The current
+ * populations are discarded: call lbm_init before the next lbm_step (LBM_ERR_STATE otherwise). */
+int lbm_set_params(lbm_ctx* ctx, double tau, const double* Theta);
+
+/* f(0) = feq(rho, u) at every fluid cell (Sec. 4 initialises from the macroscopic fields).
+ * rho: device [N] or NULL (uniform rho0); u: device [d][N] or NULL (at rest). Values at solid
+ * cells are ignored. Resets the step counter; the fields are kept for lbm_adjoint. */
+int lbm_init(lbm_ctx* ctx, const void* rho, const void* u);
+
+/* Advance n >= 0 time steps of Eq. LBE_BGK: one fused stream + collide kernel per step. */
+int lbm_step(lbm_ctx* ctx, int n);
+
+/* Macroscopic fields of f(t): rho = sum f_i, u = sum f_i c_i / rho (Eqs. a0discrete_f,
+ * a1discrete_f), Pi_ab = sum f_i c_ia c_ib. Any pointer may be NULL. Solid cells get 0. */
+int lbm_moments(lbm_ctx* ctx, void* rho, void* u, void* Pi);
+
+/* Pre-collision populations f_i(x, t) into device [q][N], in the library's direction order
+ * (lbm_lattice_info). Solid cells get 0. */
+int lbm_populations(lbm_ctx* ctx, void* f);
+
+/* FP64 totals over fluid cells: mass = sum rho, momentum[a] = sum rho u_a (host outputs; either
+ * may be NULL). Deterministic order. Synchronises. Returns LBM_ERR_UNSTABLE if any fluid cell
+ * has rho <= 0 or a non-finite moment. */
+int lbm_totals(lbm_ctx* ctx, double* mass, double* momentum);
+
+/* Discrete adjoint of f(0) = feq(rho0, u0) -> f(n) -> u(n) for a loss L(u(n)) with
+ * loss_grad = dL/du(n) (device [d][N], field type). Requires exactly n steps since the last
+ * lbm_init (else LBM_ERR_NO_FORWARD). The trajectory is recomputed from the initial fields with
+ * checkpoints every checkpoint_every steps (0: about sqrt(n)); it leaves f(n) in place.
+ * Results are read with lbm_gradients. */
+int lbm_adjoint(lbm_ctx* ctx, const void* loss_grad, int n, int checkpoint_every);
+
+/* Gradients of the last lbm_adjoint: dTheta (host, 3 values in 2D: xx, yy, xy; 6 in 3D:
+ * xx, yy, zz, xy, xz, yz; an off-diagonal entry is dL/dTheta_ab + dL/dTheta_ba), dtau (host),
+ * du0 (device [d][N], field type). Any pointer may be NULL. Synchronises. */
+int lbm_gradients(lbm_ctx* ctx, double* dTheta, double* dtau, void* du0);
+
+/* Raw state for save/resume: a header plus the stored populations. dst/src may be host or
+ * device memory. lbm_state_bytes gives the size. Restoring into a context created with the same
+ * lattice, size, storage and scheme reproduces the run bit for bit. */
+int lbm_state_bytes(const lbm_ctx* ctx, size_t* bytes);
+int lbm_get_state(lbm_ctx* ctx, void* dst, size_t bytes);
+int lbm_set_state(lbm_ctx* ctx, const void* src, size_t bytes);
+
+/* Steps taken since the last lbm_init (or restored with the state). */
+int lbm_steps_done(const lbm_ctx* ctx, long long* steps);
+
+/* Wait for the context's stream; reports asynchronous CUDA errors. */
+int lbm_sync(lbm_ctx* ctx);
+
+/* The library's velocity set: c [q][3] (ints) and w [q] (host). Returns q, or a negative
+ * status for an unknown lattice. Directions come in opposite pairs: 0 is rest, 2k+1 and 2k+2
+ * are opposite. */
+int lbm_lattice_info(int lattice, int* c, double* w);
+
+/* Bytes of library-owned device memory held by the context. */
+int lbm_device_bytes(const lbm_ctx* ctx, size_t* bytes);
+
+/* Kernel launches issued by this context since creation (all kinds). */
+int lbm_launch_count(const lbm_ctx* ctx, long long* launches);
+
+const char* lbm_status_string(int status);
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

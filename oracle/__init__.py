@@ -65,6 +65,8 @@ def _load():
             lib.oracle_totals.argtypes = [I, I, I, I, P, P, P]
             lib.oracle_adjoint.argtypes = [I, I, I, I, D, P, I, P, P, P, I, P, P, P, P]
             lib.oracle_threads.restype = I
+            lib.oracle_collide_cell.argtypes = [I, D, P, I, P, P]
+            lib.oracle_collide_cell.restype = I
             for fn in ("oracle_lattice", "oracle_feq", "oracle_init", "oracle_run", "oracle_moments",
                        "oracle_totals", "oracle_adjoint"):
                 getattr(lib, fn).restype = I
@@ -120,6 +122,17 @@ def feq(q: int, rho: float, u, Theta, order: int = 3):
     out = np.zeros(q)
     if _load().oracle_feq(q, float(rho), _ptr(u), _ptr(Th), int(order), _ptr(out)):
         raise ValueError("oracle_feq failed")
+    return out
+
+
+def collide_cell(q: int, f, tau: float, Theta, order: int = 3):
+    """Post-collision populations of one cell (oracle direction order)."""
+    d = D_OF_Q[q]
+    f = _f64(np.asarray(f).reshape(q))
+    Th = _f64(np.asarray(Theta).reshape(d, d))
+    out = np.zeros(q)
+    if _load().oracle_collide_cell(q, float(tau), _ptr(Th), int(order), _ptr(f), _ptr(out)):
+        raise ValueError("oracle_collide_cell failed")
     return out
 
 

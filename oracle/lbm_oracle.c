@@ -30,7 +30,11 @@ typedef struct {
     int c[MAXQ][3];
     double w[MAXQ];
     int opp[MAXQ];
+    /* Hermite tensors of each lattice velocity (see hermite_tensors), filled once per lattice */
+    double H1[MAXQ][3], H2[MAXQ][3][3], H3[MAXQ][3][3][3];
 } olat;
+
+static void hermite_tensors(const olat* L, int i, double H1[3], double H2[3][3], double H3[3][3][3]);
 
 /* ---------------------------------------------------------------------------------------------
  * Lattices (Appendix C). D1Q3 nodes are the roots of the probabilists' Hermite polynomial
@@ -118,6 +122,7 @@ static int build_lattice(int q, olat* L) {
     } else {
         return -1;
     }
+    for (int i = 0; i < L->q; ++i) hermite_tensors(L, i, L->H1[i], L->H2[i], L->H3[i]);
     for (int i = 0; i < L->q; ++i) {
         L->opp[i] = -1;
         for (int j = 0; j < L->q; ++j)
@@ -186,8 +191,9 @@ static void feq_cell(const olat* L, int order, double rho, const double u3[3], d
                 a3[a][b][g] = u3[a] * u3[b] * u3[g] + Kt[a][b] * u3[g] + Kt[b][g] * u3[a] + Kt[g][a] * u3[b];
         }
     for (int i = 0; i < L->q; ++i) {
-        double H1[3], H2[3][3], H3[3][3][3];
-        hermite_tensors(L, i, H1, H2, H3);
+        const double* H1 = L->H1[i];
+        const double(*H2)[3] = L->H2[i];
+        const double(*H3)[3][3] = L->H3[i];
         double s1 = 0.0, s2 = 0.0, s3 = 0.0;
         for (int a = 0; a < 3; ++a) {
             s1 += u3[a] * H1[a];
@@ -292,6 +298,19 @@ static void step_push(const olat* L, int nx, int ny, int nz, double tau, double 
                 fn[n * q + L->opp[i]] = fs;
         }
     }
+}
+
+/* Post-collision populations of one cell (oracle order): f*_i = f_i + (feq_i(m(f)) - f_i)/tau. */
+int oracle_collide_cell(int q, double tau, const double* Theta, int order, const double* f, double* fs) {
+    olat L;
+    if (build_lattice(q, &L)) return -1;
+    double Kt[3][3];
+    ktilde(&L, Theta, Kt);
+    double rho, u3[3], feq[MAXQ];
+    cell_moments(&L, f, &rho, u3);
+    feq_cell(&L, order, rho, u3, Kt, feq);
+    for (int i = 0; i < L.q; ++i) fs[i] = f[i] + (feq[i] - f[i]) / tau;
+    return 0;
 }
 
 /* Advance f ([N][q], in place) by nsteps. */
@@ -407,8 +426,9 @@ static void feq_derivs(const olat* L, int order, double rho, const double u3[3],
         for (int b = 0; b < 3; ++b) a2[a][b] = u3[a] * u3[b] + Kt[a][b];
     (void)a2;
     for (int i = 0; i < L->q; ++i) {
-        double H1[3], H2[3][3], H3[3][3][3];
-        hermite_tensors(L, i, H1, H2, H3);
+        const double* H1 = L->H1[i];
+        const double(*H2)[3] = L->H2[i];
+        const double(*H3)[3][3] = L->H3[i];
         /* d/du_e of s1, s2, s3 */
         for (int e = 0; e < 3; ++e) {
             double ds1 = H1[e];

@@ -1,0 +1,906 @@
+// C-ABI implementation of include/lbm.h: context management, parameter validation, FP64 tables,
+// the time-step loop (optionally replayed as CUDA graphs), observables, FP64 totals and the
+// checkpointed discrete adjoint. Every numerical step runs in the kernels of lbm_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+#include "lbm_lattice.cuh"
+
+namespace lbm {
+
+Shape shape_for(const Geom& g) {
+    Shape s;
+    const int bx = std::min(256, ((g.nx + 31) / 32) * 32);
+    const int by = std::max(1, 256 / bx);
+    s.block = dim3(bx, by, 1);
+    s.grid = dim3((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
+    s.nblocks = (long long)s.grid.x * s.grid.y * s.grid.z;
+    return s;
+}
+
+// Fixed-order FP64 sum: thread t adds records t, t + 1024, ... in order, then a fixed tree.
+__global__ void __launch_bounds__(1024) k_reduce_partials(const double* __restrict__ part, long long nb, int width,
+                                                          double* __restrict__ out) {
+    __shared__ double sh[1024];
+    for (int k = 0; k < width; ++k) {
+        double s = 0.0;
+        for (long long b = threadIdx.x; b < nb; b += blockDim.x) s += part[b * width + k];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[k] = sh[0];
+        __syncthreads();
+    }
+}
+
+cudaError_t reduce_partials(const double* partials, long long nb, int width, double* out, cudaStream_t s) {
+    k_reduce_partials<<<1, 1024, 0, s>>>(partials, nb, width, out);
+    return cudaGetLastError();
+}
+
+static const Ops* ops_get(int q, int storage) {
+#define LBM_PICK(Q)                              \
+    switch (storage) {                           \
+        case 0: return &ops_q##Q##_s0();         \
+        case 1: return &ops_q##Q##_s1();         \
+        case 2: return &ops_q##Q##_s2();         \
+        case 3: return &ops_q##Q##_s3();         \
+        default: return nullptr;                 \
+    }
+    if (q == 9) LBM_PICK(9)
+    if (q == 19) LBM_PICK(19)
+    if (q == 27) LBM_PICK(27)
+#undef LBM_PICK
+    return nullptr;
+}
+
+template <int Q>
+static Vec3 hvel(int i) {
+    return vel<Q>(i);
+}
+template <int Q>
+static double hweight(int i) {
+    return weight<Q>(i);
+}
+static Vec3 velq(int q, int i) { return q == 9 ? hvel<9>(i) : q == 19 ? hvel<19>(i) : hvel<27>(i); }
+static double weightq(int q, int i) { return q == 9 ? hweight<9>(i) : q == 19 ? hweight<19>(i) : hweight<27>(i); }
+
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_ctx {
+    int q = 0, d = 0, nx = 0, ny = 0, nz = 0;
+    long long N = 0;
+    double tau = 0.0;
+    double Theta[9] = {0};
+    lbm_options opt{};
+    int storage = 0, scheme = 0, order = 3;
+    size_t elem = 4;   // bytes per stored population
+    size_t felem = 4;  // bytes per field value (float or double)
+    const Ops* ops = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+
+    Geom geom{};
+    Shape shape{};
+    uint32_t* mask = nullptr;
+    long long n_fluid = 0;
+
+    Coef<double> cd{};
+    Coef<float> cf{};
+
+    void* pop[2] = {nullptr, nullptr};
+    int cur = 0;          // pull scheme: buffer holding the current state
+    long long steps = 0;  // steps since init
+    bool state_valid = false;
+    bool init_fields = false;  // rho0/u0 copies are present for the adjoint
+    void* rho_init = nullptr;
+    void* u_init = nullptr;
+    bool rho_init_null = true, u_init_null = true;
+
+    int* flag = nullptr;
+    double* partials = nullptr;  // nblocks * 8
+    double* dout = nullptr;      // 8 doubles
+    double* hout = nullptr;      // pinned 8 doubles
+    int* hflag = nullptr;        // pinned
+
+    // adjoint
+    void* lam[2] = {nullptr, nullptr};
+    void* du0 = nullptr;
+    double* gpart = nullptr;
+    bool grads_ready = false;
+    double grad_theta[6] = {0};
+    double grad_tau = 0.0;
+
+    // graphs
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+
+    size_t dev_bytes = 0;
+    long long launches = 0;
+    std::string err;
+
+    const void* coef() const { return storage == LBM_FP64 ? (const void*)&cd : (const void*)&cf; }
+    size_t state_bytes() const { return (size_t)q * (size_t)N * elem; }
+};
+
+namespace {
+
+int fail(lbm_ctx* c, int code, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, LBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(ctx, call)                                       \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+void* dev_alloc(lbm_ctx* c, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (c->opt.alloc) {
+        p = c->opt.alloc(bytes, c->opt.alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->dev_bytes += bytes;
+    return p;
+}
+
+void dev_free(lbm_ctx* c, void* p, size_t bytes) {
+    if (!p) return;
+    if (c->opt.alloc)
+        c->opt.free(p, c->opt.alloc_user);
+    else
+        cudaFree(p);
+    c->dev_bytes -= bytes;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Symmetric positive definite check by FP64 Cholesky.
+int check_theta(lbm_ctx* c, int d, const double* Th) {
+    if (!Th) return fail(c, LBM_ERR_INVALID_ARG, "Theta is NULL");
+    double scale = 0.0;
+    for (int k = 0; k < d * d; ++k) {
+        if (!std::isfinite(Th[k])) return fail(c, LBM_ERR_INVALID_ARG, "Theta has a non-finite entry");
+        scale = std::max(scale, std::fabs(Th[k]));
+    }
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < a; ++b)
+            if (std::fabs(Th[a * d + b] - Th[b * d + a]) > 1e-12 * std::max(1.0, scale))
+                return fail(c, LBM_ERR_NOT_SPD, "Theta is not symmetric");
+    double L[3][3] = {{0}};
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = Th[i * d + j];
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(s > 0.0)) return fail(c, LBM_ERR_NOT_SPD, "Theta is not positive definite");
+                L[i][i] = std::sqrt(s);
+            } else {
+                L[i][j] = s / L[j][j];
+            }
+        }
+    return LBM_OK;
+}
+
+// FP64 coefficient tables for (tau, Theta, rho0, order), then one rounding to FP32.
+void build_coef(lbm_ctx* c) {
+    const int q = c->q, d = c->d;
+    const double cs2 = 1.0 / 3.0;
+    double Kt[3][3] = {{0}};
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) Kt[a][b] = c->Theta[a * d + b] - (a == b ? cs2 : 0.0);
+    double trK = 0.0;
+    for (int a = 0; a < d; ++a) trK += Kt[a][a];
+    Coef<double>& C = c->cd;
+    std::memset(&C, 0, sizeof(C));
+    const double rho0 = c->opt.rho0;
+    C.omega = 1.0 / c->tau;
+    C.rho0 = rho0;
+    C.c3 = c->order == 3 ? 4.5 : 0.0;
+    C.K[0] = Kt[0][0];
+    C.K[1] = Kt[1][1];
+    C.K[2] = Kt[2][2];
+    C.K[3] = Kt[0][1];
+    C.K[4] = Kt[0][2];
+    C.K[5] = Kt[1][2];
+    const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
+    for (int i = 0; i < q; ++i) {
+        const Vec3 v = velq(q, i);
+        const double cv[3] = {(double)v.x, (double)v.y, (double)v.z};
+        double h = -cs2 * trK;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) h += cv[a] * Kt[a][b] * cv[b];
+        const double w = weightq(q, i);
+        C.h[i] = h;
+        C.A[i] = w * (1.0 + 4.5 * h);
+        C.r[i] = rho0 * C.A[i];
+        C.B[i] = w * (3.0 + 3.0 * C.c3 * h);
+        for (int k = 0; k < 6; ++k) C.Pirest[k] += C.r[i] * cv[pa[k]] * cv[pb[k]];
+    }
+    Coef<float>& F = c->cf;
+    F.omega = (float)C.omega;
+    F.rho0 = (float)C.rho0;
+    F.c3 = (float)C.c3;
+    for (int k = 0; k < 6; ++k) {
+        F.K[k] = (float)C.K[k];
+        F.Pirest[k] = (float)C.Pirest[k];
+    }
+    for (int i = 0; i < 27; ++i) {
+        F.r[i] = (float)C.r[i];
+        F.A[i] = (float)C.A[i];
+        F.B[i] = (float)C.B[i];
+        F.h[i] = (float)C.h[i];
+    }
+}
+
+void drop_graph(lbm_ctx* c) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    c->graph_steps = 0;
+}
+
+int layout_now(const lbm_ctx* c, long long steps) {
+    if (c->scheme == LBM_PULL2) return LAYOUT_PULL;
+    return (steps & 1) ? LAYOUT_AAODD : LAYOUT_LOCAL;
+}
+
+void* state_ptr(lbm_ctx* c) { return c->scheme == LBM_PULL2 ? c->pop[c->cur] : c->pop[0]; }
+
+// One time step from the current state, on stream s. Advances cur/steps.
+cudaError_t launch_step(lbm_ctx* c, cudaStream_t s) {
+    cudaError_t e;
+    if (c->scheme == LBM_PULL2) {
+        e = c->ops->step_pull(c->geom, c->coef(), c->pop[c->cur], c->pop[c->cur ^ 1], c->flag, s);
+        c->cur ^= 1;
+    } else {
+        e = c->ops->step_aa(c->geom, c->coef(), (int)(c->steps & 1), c->pop[0], c->pop[0], c->flag, s);
+    }
+    c->steps += 1;
+    c->launches += 1;
+    return e;
+}
+
+int ensure_graph(lbm_ctx* c, int gsteps) {
+    if (c->graph && c->graph_steps == gsteps) return LBM_OK;
+    drop_graph(c);
+    if (!c->cap_stream) LBM_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    const int cur0 = c->cur;
+    const long long steps0 = c->steps;
+    const long long launches0 = c->launches;
+    LBM_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < gsteps && le == cudaSuccess; ++k) le = launch_step(c, c->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &g);
+    c->cur = cur0;
+    c->steps = steps0;
+    c->launches = launches0;
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, le, "kernel launch during graph capture");
+    }
+    if (ee != cudaSuccess) return cuda_fail(c, ee, "cudaStreamEndCapture");
+    cudaError_t ie = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        c->graph = nullptr;
+        return cuda_fail(c, ie, "cudaGraphInstantiate");
+    }
+    c->graph_steps = gsteps;
+    return LBM_OK;
+}
+
+int check_flag(lbm_ctx* c) {
+    LBM_CUDA(c, cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (*c->hflag) return fail(c, LBM_ERR_UNSTABLE, "a fluid cell reached rho <= 0 or a non-finite value");
+    return LBM_OK;
+}
+
+}  // namespace
+
+// =============================================================================================
+extern "C" {
+
+int lbm_options_default(lbm_options* opt) {
+    if (!opt) return LBM_ERR_INVALID_ARG;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->storage = LBM_FP32;
+    opt->scheme = LBM_PULL2;
+    opt->order = 3;
+    opt->rho0 = 1.0;
+    return LBM_OK;
+}
+
+const char* lbm_status_string(int s) {
+    switch (s) {
+        case LBM_OK: return "ok";
+        case LBM_ERR_INVALID_ARG: return "invalid argument";
+        case LBM_ERR_NOT_SPD: return "Theta is not symmetric positive definite";
+        case LBM_ERR_BAD_TAU: return "tau must exceed 1/2";
+        case LBM_ERR_OOM: return "out of memory";
+        case LBM_ERR_CUDA: return "CUDA error";
+        case LBM_ERR_UNSTABLE: return "simulation became unstable";
+        case LBM_ERR_NO_FORWARD: return "adjoint needs exactly n forward steps since lbm_init";
+        case LBM_ERR_TIMEOUT: return "device wait timed out";
+        case LBM_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : "no context"; }
+
+int lbm_lattice_info(int lattice, int* c, double* w) {
+    if (lattice != 9 && lattice != 19 && lattice != 27) return LBM_ERR_INVALID_ARG;
+    for (int i = 0; i < lattice; ++i) {
+        const Vec3 v = velq(lattice, i);
+        if (c) {
+            c[3 * i] = v.x;
+            c[3 * i + 1] = v.y;
+            c[3 * i + 2] = v.z;
+        }
+        if (w) w[i] = weightq(lattice, i);
+    }
+    return lattice;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    drop_graph(c);
+    const size_t SB = c->state_bytes();
+    dev_free(c, c->pop[0], SB);
+    dev_free(c, c->pop[1], SB);
+    dev_free(c, c->mask, (size_t)c->geom.W * c->ny * c->nz * 4);
+    dev_free(c, c->rho_init, (size_t)c->N * c->felem);
+    dev_free(c, c->u_init, (size_t)c->N * c->d * c->felem);
+    dev_free(c, c->flag, sizeof(int) * 2);
+    dev_free(c, c->partials, (size_t)c->shape.nblocks * 8 * sizeof(double));
+    dev_free(c, c->dout, 8 * sizeof(double));
+    const size_t LB = (size_t)c->q * c->N * c->felem;
+    dev_free(c, c->lam[0], LB);
+    dev_free(c, c->lam[1], LB);
+    dev_free(c, c->du0, (size_t)c->d * c->N * c->felem);
+    dev_free(c, c->gpart, (size_t)c->shape.nblocks * 8 * sizeof(double));
+    if (c->hout) cudaFreeHost(c->hout);
+    if (c->hflag) cudaFreeHost(c->hflag);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau, const double* Theta,
+                  const uint8_t* solid_mask, const lbm_options* opt) {
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_ERR_OOM;
+    auto bail = [&](int code) {
+        std::string keep = c->err;
+        lbm_destroy(c);
+        (void)keep;
+        return code;
+    };
+    if (opt)
+        c->opt = *opt;
+    else
+        lbm_options_default(&c->opt);
+    if (c->opt.order == 0) c->opt.order = 3;
+    if (c->opt.rho0 == 0.0) c->opt.rho0 = 1.0;
+    if (lattice != 9 && lattice != 19 && lattice != 27) return bail(LBM_ERR_INVALID_ARG);
+    if (c->opt.storage < 0 || c->opt.storage > 3 || c->opt.scheme < 0 || c->opt.scheme > 1) return bail(LBM_ERR_INVALID_ARG);
+    if (c->opt.order != 2 && c->opt.order != 3) return bail(LBM_ERR_INVALID_ARG);
+    if (!(c->opt.rho0 > 0.0) || !std::isfinite(c->opt.rho0)) return bail(LBM_ERR_INVALID_ARG);
+    if ((c->opt.alloc == nullptr) != (c->opt.free == nullptr)) return bail(LBM_ERR_INVALID_ARG);
+    c->q = lattice;
+    c->d = lattice == 9 ? 2 : 3;
+    if (nx < 1 || ny < 1 || nz < 1 || (c->d == 2 && nz != 1)) return bail(LBM_ERR_INVALID_ARG);
+    {
+        Geom g0{};
+        g0.nx = nx;
+        g0.ny = ny;
+        g0.nz = nz;
+        const Shape s0 = shape_for(g0);
+        if (nz > 65535 || s0.grid.y > 65535u) return bail(LBM_ERR_INVALID_ARG);
+    }
+    if (!(tau > 0.5) || !std::isfinite(tau)) return bail(LBM_ERR_BAD_TAU);
+    int rc = check_theta(c, c->d, Theta);
+    if (rc) return bail(rc);
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->N = (long long)nx * ny * nz;
+    c->tau = tau;
+    for (int k = 0; k < c->d * c->d; ++k) c->Theta[k] = Theta[k];
+    c->storage = c->opt.storage;
+    c->scheme = c->opt.scheme;
+    c->order = c->opt.order;
+    c->elem = c->storage == LBM_FP64 ? 8 : c->storage == LBM_FP16_SHIFTED ? 2 : 4;
+    c->felem = c->storage == LBM_FP64 ? 8 : 4;
+    c->ops = ops_get(c->q, c->storage);
+    c->stream = (cudaStream_t)c->opt.stream;
+    build_coef(c);
+
+    c->geom.nx = nx;
+    c->geom.ny = ny;
+    c->geom.nz = nz;
+    c->geom.N = c->N;
+    c->geom.W = (nx + 31) / 32;
+    c->geom.mask = nullptr;
+    c->shape = shape_for(c->geom);
+    c->n_fluid = c->N;
+
+    if (solid_mask) {
+        std::vector<uint8_t> m((size_t)c->N);
+        if (is_device_ptr(solid_mask)) {
+            if (cudaMemcpy(m.data(), solid_mask, (size_t)c->N, cudaMemcpyDeviceToHost) != cudaSuccess)
+                return bail(cuda_fail(c, cudaGetLastError(), "copy of the solid mask"));
+        } else {
+            std::memcpy(m.data(), solid_mask, (size_t)c->N);
+        }
+        const size_t rows = (size_t)ny * nz, W = (size_t)c->geom.W;
+        std::vector<uint32_t> bits(rows * W, 0u);
+        long long nsolid = 0;
+        for (size_t r = 0; r < rows; ++r)
+            for (int x = 0; x < nx; ++x)
+                if (m[r * nx + x]) {
+                    bits[r * W + x / 32] |= 1u << (x % 32);
+                    ++nsolid;
+                }
+        c->n_fluid = c->N - nsolid;
+        if (nsolid > 0) {
+            c->mask = (uint32_t*)dev_alloc(c, rows * W * 4);
+            if (!c->mask) return bail(fail(c, LBM_ERR_OOM, "mask allocation"));
+            if (cudaMemcpy(c->mask, bits.data(), rows * W * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+                return bail(cuda_fail(c, cudaGetLastError(), "mask upload"));
+            c->geom.mask = c->mask;
+        }
+    }
+    const size_t SB = c->state_bytes();
+    c->pop[0] = dev_alloc(c, SB);
+    if (c->scheme == LBM_PULL2) c->pop[1] = dev_alloc(c, SB);
+    c->flag = (int*)dev_alloc(c, sizeof(int) * 2);
+    c->partials = (double*)dev_alloc(c, (size_t)c->shape.nblocks * 8 * sizeof(double));
+    c->dout = (double*)dev_alloc(c, 8 * sizeof(double));
+    if (!c->pop[0] || (c->scheme == LBM_PULL2 && !c->pop[1]) || !c->flag || !c->partials || !c->dout)
+        return bail(fail(c, LBM_ERR_OOM, "population allocation (%zu bytes per array)", SB));
+    if (cudaMallocHost(&c->hout, 8 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&c->hflag, 2 * sizeof(int)) != cudaSuccess)
+        return bail(fail(c, LBM_ERR_OOM, "pinned host allocation"));
+    // solid-cell slots are never written by the kernels; keep them defined
+    if (cudaMemsetAsync(c->pop[0], 0, SB, c->stream) != cudaSuccess ||
+        (c->pop[1] && cudaMemsetAsync(c->pop[1], 0, SB, c->stream) != cudaSuccess) ||
+        cudaMemsetAsync(c->flag, 0, sizeof(int) * 2, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return bail(cuda_fail(c, cudaGetLastError(), "buffer clear"));
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau, const double* Theta,
+               const uint8_t* solid_mask) {
+    return lbm_create_ex(out, lattice, nx, ny, nz, tau, Theta, solid_mask, nullptr);
+}
+
+int lbm_set_params(lbm_ctx* c, double tau, const double* Theta) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (!(tau > 0.5) || !std::isfinite(tau)) return fail(c, LBM_ERR_BAD_TAU, "tau = %g", tau);
+    int rc = check_theta(c, c->d, Theta);
+    if (rc) return rc;
+    c->tau = tau;
+    for (int k = 0; k < c->d * c->d; ++k) c->Theta[k] = Theta[k];
+    build_coef(c);
+    drop_graph(c);
+    c->state_valid = false;
+    c->init_fields = false;
+    c->grads_ready = false;
+    return LBM_OK;
+}
+
+int lbm_init(lbm_ctx* c, const void* rho, const void* u) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    const size_t FN = (size_t)c->N * c->felem;
+    if (!c->rho_init) c->rho_init = dev_alloc(c, FN);
+    if (!c->u_init) c->u_init = dev_alloc(c, FN * c->d);
+    if (!c->rho_init || !c->u_init) return fail(c, LBM_ERR_OOM, "initial-field copies");
+    if (rho) LBM_CUDA(c, cudaMemcpyAsync(c->rho_init, rho, FN, cudaMemcpyDefault, c->stream));
+    if (u) LBM_CUDA(c, cudaMemcpyAsync(c->u_init, u, FN * c->d, cudaMemcpyDefault, c->stream));
+    c->rho_init_null = rho == nullptr;
+    c->u_init_null = u == nullptr;
+    c->cur = 0;
+    c->steps = 0;
+    const int layout = c->scheme == LBM_PULL2 ? LAYOUT_PULL : LAYOUT_LOCAL;
+    cudaError_t e = c->ops->init(c->geom, c->coef(), layout, rho ? c->rho_init : nullptr, u ? c->u_init : nullptr,
+                                 c->pop[0], c->stream);
+    c->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    LBM_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    c->state_valid = true;
+    c->init_fields = true;
+    c->grads_ready = false;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int n) {
+    if (!c || n < 0) return LBM_ERR_INVALID_ARG;
+    if (!c->state_valid) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init");
+    const int gsteps = 16;
+    bool graphs = c->opt.use_graphs > 0 || (c->opt.use_graphs == 0 && c->N <= (1LL << 21));
+    long long next_check = c->opt.check_every > 0 ? (c->steps / c->opt.check_every + 1) * c->opt.check_every : -1;
+    int left = n;
+    while (left > 0) {
+        const bool aligned = (c->steps & 1) == 0 && (c->scheme != LBM_PULL2 || c->cur == 0);
+        bool ran = false;
+        if (graphs && left >= gsteps && aligned &&
+            (next_check < 0 || c->steps + gsteps <= next_check)) {
+            int rc = ensure_graph(c, gsteps);
+            if (rc) return rc;
+            LBM_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
+            c->steps += gsteps;
+            c->launches += gsteps;
+            left -= gsteps;
+            ran = true;
+        }
+        if (!ran) {
+            cudaError_t e = launch_step(c, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "stream-collide kernel");
+            left -= 1;
+        }
+        if (next_check >= 0 && c->steps >= next_check) {
+            int rc = check_flag(c);
+            if (rc) return rc;
+            next_check += c->opt.check_every;
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx* c, void* rho, void* u, void* Pi) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (!c->state_valid) return fail(c, LBM_ERR_STATE, "lbm_moments before lbm_init");
+    if (!rho && !u && !Pi) return LBM_OK;
+    cudaError_t e = c->ops->moments(c->geom, c->coef(), layout_now(c, c->steps), state_ptr(c), rho, u, Pi, nullptr,
+                                    c->stream);
+    c->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel");
+    return LBM_OK;
+}
+
+int lbm_populations(lbm_ctx* c, void* f) {
+    if (!c || !f) return LBM_ERR_INVALID_ARG;
+    if (!c->state_valid) return fail(c, LBM_ERR_STATE, "lbm_populations before lbm_init");
+    cudaError_t e = c->ops->moments(c->geom, c->coef(), layout_now(c, c->steps), state_ptr(c), nullptr, nullptr,
+                                    nullptr, f, c->stream);
+    c->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(c, e, "populations kernel");
+    return LBM_OK;
+}
+
+int lbm_totals(lbm_ctx* c, double* mass, double* momentum) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (!c->state_valid) return fail(c, LBM_ERR_STATE, "lbm_totals before lbm_init");
+    LBM_CUDA(c, cudaMemsetAsync(c->flag + 1, 0, sizeof(int), c->stream));
+    cudaError_t e = c->ops->totals(c->geom, c->coef(), layout_now(c, c->steps), state_ptr(c), c->partials,
+                                   c->flag + 1, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "totals kernel");
+    e = reduce_partials(c->partials, c->shape.nblocks, 4, c->dout, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "totals reduction");
+    c->launches += 2;
+    LBM_CUDA(c, cudaMemcpyAsync(c->hout, c->dout, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaMemcpyAsync(c->hflag + 1, c->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (mass) *mass = c->hout[0];
+    if (momentum)
+        for (int a = 0; a < c->d; ++a) momentum[a] = c->hout[1 + a];
+    if (c->hflag[1]) return fail(c, LBM_ERR_UNSTABLE, "a fluid cell has rho <= 0 or a non-finite moment");
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Discrete adjoint with checkpointing. States are kept in the stored form, so a recomputed
+// state is bit-identical to the forward one.
+// ---------------------------------------------------------------------------------------------
+int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
+    if (!c || !loss_grad || n < 0 || K < 0) return LBM_ERR_INVALID_ARG;
+    if (!c->init_fields || !c->state_valid || c->steps != n)
+        return fail(c, LBM_ERR_NO_FORWARD, "adjoint over %d steps but %lld steps were run since lbm_init", n,
+                    (long long)c->steps);
+    if (K == 0) K = std::max(1, (int)std::lround(std::sqrt((double)std::max(n, 1))));
+    K = std::max(1, std::min(K, std::max(n, 1)));
+    const size_t SB = c->state_bytes();
+    const size_t LB = (size_t)c->q * c->N * c->felem;
+    const size_t GB = (size_t)c->shape.nblocks * 8 * sizeof(double);
+    if (!c->lam[0]) {
+        c->lam[0] = dev_alloc(c, LB);
+        c->lam[1] = dev_alloc(c, LB);
+        c->du0 = dev_alloc(c, (size_t)c->d * c->N * c->felem);
+        c->gpart = (double*)dev_alloc(c, GB);
+        if (!c->lam[0] || !c->lam[1] || !c->du0 || !c->gpart) return fail(c, LBM_ERR_OOM, "adjoint buffers");
+        LBM_CUDA(c, cudaMemsetAsync(c->lam[0], 0, LB, c->stream));
+        LBM_CUDA(c, cudaMemsetAsync(c->lam[1], 0, LB, c->stream));
+    }
+    LBM_CUDA(c, cudaMemsetAsync(c->gpart, 0, GB, c->stream));
+    c->grads_ready = false;
+
+    const int C = (n + K - 1) / K;  // checkpoints at t = 0, K, ..., (C-1)K
+    // Memory: C checkpoints + (K - 1) segment states + 2 stepping buffers.
+    size_t limit = c->opt.adjoint_mem_limit;
+    if (limit == 0) {
+        size_t fr = 0, tot = 0;
+        LBM_CUDA(c, cudaMemGetInfo(&fr, &tot));
+        const size_t margin = (size_t)2 << 30;
+        limit = fr > margin ? fr - margin : 0;
+    }
+    const int nseg = std::max(K - 1, 0);
+    const int nstep_buf = 2;
+    const bool ckpt_on_device = (size_t)(C + nseg + nstep_buf) * SB <= limit;
+    if ((size_t)(nseg + nstep_buf) * SB > limit)
+        return fail(c, LBM_ERR_OOM, "adjoint segment of %d states (%zu bytes each) exceeds the memory limit", K, SB);
+
+    std::vector<void*> ckpt(C, nullptr), seg(nseg, nullptr);
+    void* stepbuf[2] = {nullptr, nullptr};
+    bool host_ckpt = !ckpt_on_device;
+    int rc = LBM_OK;
+    auto release = [&]() {
+        cudaStreamSynchronize(c->stream);
+        for (void* p : ckpt)
+            if (p) {
+                if (host_ckpt)
+                    cudaFreeHost(p);
+                else
+                    dev_free(c, p, SB);
+            }
+        for (void* p : seg) dev_free(c, p, SB);
+        dev_free(c, stepbuf[0], SB);
+        dev_free(c, stepbuf[1], SB);
+    };
+    for (int k = 0; k < C; ++k) {
+        if (host_ckpt) {
+            if (cudaMallocHost(&ckpt[k], SB) != cudaSuccess) {
+                ckpt[k] = nullptr;
+                release();
+                return fail(c, LBM_ERR_OOM, "host checkpoint %d of %zu bytes", k, SB);
+            }
+        } else if (!(ckpt[k] = dev_alloc(c, SB))) {
+            release();
+            return fail(c, LBM_ERR_OOM, "device checkpoint %d", k);
+        }
+    }
+    for (int k = 0; k < nseg; ++k)
+        if (!(seg[k] = dev_alloc(c, SB))) {
+            release();
+            return fail(c, LBM_ERR_OOM, "segment state %d", k);
+        }
+    stepbuf[0] = dev_alloc(c, SB);
+    stepbuf[1] = dev_alloc(c, SB);
+    if (!stepbuf[0] || !stepbuf[1]) {
+        release();
+        return fail(c, LBM_ERR_OOM, "adjoint stepping buffers");
+    }
+    for (int k = 0; k < 2; ++k)
+        if (cudaMemsetAsync(stepbuf[k], 0, SB, c->stream) != cudaSuccess) {
+            release();
+            return cuda_fail(c, cudaGetLastError(), "clear stepping buffer");
+        }
+    for (int k = 0; k < nseg; ++k)
+        if (cudaMemsetAsync(seg[k], 0, SB, c->stream) != cudaSuccess) {
+            release();
+            return cuda_fail(c, cudaGetLastError(), "clear segment buffer");
+        }
+
+    const void* cf = c->coef();
+    // out-of-place step t -> t+1 from src to dst
+    auto step_oop = [&](const void* src, void* dst, long long t) -> cudaError_t {
+        c->launches += 1;
+        if (c->scheme == LBM_PULL2) return c->ops->step_pull(c->geom, cf, src, dst, c->flag, c->stream);
+        return c->ops->step_aa(c->geom, cf, (int)(t & 1), src, dst, c->flag, c->stream);
+    };
+    auto layout_at = [&](long long t) { return layout_now(c, t); };
+
+#define LBM_ADJ_CHECK(expr, what)                       \
+    do {                                                \
+        cudaError_t e_ = (expr);                        \
+        if (e_ != cudaSuccess) {                        \
+            rc = cuda_fail(c, e_, what);                \
+            release();                                  \
+            return rc;                                  \
+        }                                               \
+    } while (0)
+
+    // Forward pass from the initial fields: checkpoints at multiples of K.
+    const int init_layout = c->scheme == LBM_PULL2 ? LAYOUT_PULL : LAYOUT_LOCAL;
+    LBM_ADJ_CHECK(c->ops->init(c->geom, cf, init_layout, c->rho_init_null ? nullptr : c->rho_init,
+                               c->u_init_null ? nullptr : c->u_init, stepbuf[0], c->stream),
+                  "adjoint init");
+    c->launches += 1;
+    int sb = 0;
+    for (long long t = 0; t <= n; ++t) {
+        if (t % K == 0 && t < n) {
+            const int k = (int)(t / K);
+            LBM_ADJ_CHECK(cudaMemcpyAsync(ckpt[k], stepbuf[sb], SB, cudaMemcpyDefault, c->stream), "checkpoint copy");
+        }
+        if (t == n) break;
+        LBM_ADJ_CHECK(step_oop(stepbuf[sb], stepbuf[sb ^ 1], t), "forward recompute");
+        sb ^= 1;
+    }
+    // seed from f(n)
+    int lc = 0;
+    LBM_ADJ_CHECK(c->ops->adj_seed(c->geom, cf, layout_at(n), stepbuf[sb], loss_grad, c->lam[lc], c->stream),
+                  "adjoint seed");
+    c->launches += 1;
+    // Reverse sweep over segments.
+    for (int s = C - 1; s >= 0; --s) {
+        const long long t0 = (long long)s * K;
+        const int len = (int)std::min<long long>(K, n - t0);
+        // states t0 .. t0+len-1: state(t0) in stepbuf[0], state(t0+j) in seg[j-1]
+        LBM_ADJ_CHECK(cudaMemcpyAsync(stepbuf[0], ckpt[s], SB, cudaMemcpyDefault, c->stream), "checkpoint restore");
+        for (int j = 1; j < len; ++j) {
+            const void* src = j == 1 ? stepbuf[0] : seg[j - 2];
+            LBM_ADJ_CHECK(step_oop(src, seg[j - 1], t0 + j - 1), "segment recompute");
+        }
+        for (int j = len - 1; j >= 0; --j) {
+            const void* ft = j == 0 ? stepbuf[0] : seg[j - 1];
+            LBM_ADJ_CHECK(c->ops->adj_step(c->geom, cf, layout_at(t0 + j), ft, c->lam[lc], c->lam[lc ^ 1], c->gpart,
+                                           c->stream),
+                          "adjoint step");
+            c->launches += 1;
+            lc ^= 1;
+        }
+    }
+    // Through f(0) = feq(rho0, u0; Theta).
+    LBM_ADJ_CHECK(c->ops->adj_init(c->geom, cf, c->rho_init_null ? nullptr : c->rho_init,
+                                   c->u_init_null ? nullptr : c->u_init, c->lam[lc], c->du0, c->gpart, c->stream),
+                  "adjoint init gradient");
+    LBM_ADJ_CHECK(reduce_partials(c->gpart, c->shape.nblocks, 8, c->dout, c->stream), "gradient reduction");
+    c->launches += 2;
+    LBM_ADJ_CHECK(cudaMemcpyAsync(c->hout, c->dout, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                  "gradient copy");
+    LBM_ADJ_CHECK(cudaStreamSynchronize(c->stream), "adjoint sync");
+#undef LBM_ADJ_CHECK
+    if (c->d == 3) {
+        for (int k = 0; k < 6; ++k) c->grad_theta[k] = c->hout[k];
+    } else {
+        c->grad_theta[0] = c->hout[0];
+        c->grad_theta[1] = c->hout[1];
+        c->grad_theta[2] = c->hout[3];
+    }
+    c->grad_tau = c->hout[6];
+    c->grads_ready = true;
+    release();
+    return LBM_OK;
+}
+
+int lbm_gradients(lbm_ctx* c, double* dTheta, double* dtau, void* du0) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (!c->grads_ready) return fail(c, LBM_ERR_STATE, "lbm_gradients before a successful lbm_adjoint");
+    if (dTheta)
+        for (int k = 0; k < (c->d == 3 ? 6 : 3); ++k) dTheta[k] = c->grad_theta[k];
+    if (dtau) *dtau = c->grad_tau;
+    if (du0) {
+        LBM_CUDA(c, cudaMemcpyAsync(du0, c->du0, (size_t)c->d * c->N * c->felem, cudaMemcpyDefault, c->stream));
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Save / resume
+// ---------------------------------------------------------------------------------------------
+struct lbm_state_header {
+    char magic[8];
+    int32_t version, lattice, nx, ny, nz, storage, scheme, order;
+    int64_t steps;
+    int64_t reserved[4];
+};
+
+int lbm_state_bytes(const lbm_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return LBM_ERR_INVALID_ARG;
+    *bytes = sizeof(lbm_state_header) + c->state_bytes();
+    return LBM_OK;
+}
+
+int lbm_get_state(lbm_ctx* c, void* dst, size_t bytes) {
+    if (!c || !dst) return LBM_ERR_INVALID_ARG;
+    if (!c->state_valid) return fail(c, LBM_ERR_STATE, "no state to save");
+    if (bytes < sizeof(lbm_state_header) + c->state_bytes()) return fail(c, LBM_ERR_INVALID_ARG, "buffer too small");
+    lbm_state_header h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "LBMSTAT", 8);
+    h.version = 1;
+    h.lattice = c->q;
+    h.nx = c->nx;
+    h.ny = c->ny;
+    h.nz = c->nz;
+    h.storage = c->storage;
+    h.scheme = c->scheme;
+    h.order = c->order;
+    h.steps = c->steps;
+    LBM_CUDA(c, cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyDefault, c->stream));
+    LBM_CUDA(c, cudaMemcpyAsync((char*)dst + sizeof(h), state_ptr(c), c->state_bytes(), cudaMemcpyDefault,
+                                c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_set_state(lbm_ctx* c, const void* src, size_t bytes) {
+    if (!c || !src) return LBM_ERR_INVALID_ARG;
+    if (bytes < sizeof(lbm_state_header) + c->state_bytes()) return fail(c, LBM_ERR_INVALID_ARG, "buffer too small");
+    lbm_state_header h;
+    LBM_CUDA(c, cudaMemcpy(&h, src, sizeof(h), cudaMemcpyDefault));
+    if (std::memcmp(h.magic, "LBMSTAT", 8) != 0 || h.version != 1 || h.lattice != c->q || h.nx != c->nx ||
+        h.ny != c->ny || h.nz != c->nz || h.storage != c->storage || h.scheme != c->scheme)
+        return fail(c, LBM_ERR_INVALID_ARG, "state does not match this context");
+    c->cur = 0;
+    LBM_CUDA(c, cudaMemcpyAsync(c->pop[0], (const char*)src + sizeof(h), c->state_bytes(), cudaMemcpyDefault,
+                                c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->steps = h.steps;
+    c->state_valid = true;
+    c->init_fields = false;  // the adjoint needs the initial fields of an lbm_init
+    c->grads_ready = false;
+    return LBM_OK;
+}
+
+int lbm_steps_done(const lbm_ctx* c, long long* steps) {
+    if (!c || !steps) return LBM_ERR_INVALID_ARG;
+    *steps = c->steps;
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_ctx* c) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    LBM_CUDA(c, cudaGetLastError());
+    return LBM_OK;
+}
+
+int lbm_device_bytes(const lbm_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return LBM_ERR_INVALID_ARG;
+    *bytes = c->dev_bytes;
+    return LBM_OK;
+}
+
+int lbm_launch_count(const lbm_ctx* c, long long* launches) {
+    if (!c || !launches) return LBM_ERR_INVALID_ARG;
+    *launches = c->launches;
+    return LBM_OK;
+}
+
+}  // extern "C"

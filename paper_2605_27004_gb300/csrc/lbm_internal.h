@@ -1,0 +1,77 @@
+// Internal interface between the C-ABI host code (lbm_host.cu) and the per-lattice kernel
+// translation units (lbm_d2q9.cu, lbm_d3q19.cu, lbm_d3q27.cu). Not installed, not public.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// Grid geometry as every kernel sees it.
+struct Geom {
+    int nx, ny, nz;
+    long long N;           // nx*ny*nz
+    const uint32_t* mask;  // bit-packed solid mask (bit x%32 of word x/32 of row y+ny*z), or null
+    int W;                 // mask words per row = ceil(nx/32)
+};
+
+// Per-run constants, derived on the host in FP64 from (tau, Theta, rho0, order) and rounded
+// once to the arithmetic type T. Arrays are indexed by the library's direction order.
+template <typename T>
+struct Coef {
+    T omega;      // 1/tau
+    T rho0;       // reference density of the shifted representation
+    T c3;         // 9/2 for the third-order equilibrium, 0 for the second order
+    T K[6];       // K~ = Theta - cs2 I: xx, yy, zz, xy, xz, yz
+    T r[27];      // rest equilibrium r_i = w_i rho0 (1 + 9/2 h_i)
+    T A[27];      // w_i (1 + 9/2 h_i): density coefficient of the even part
+    T B[27];      // w_i (3 + 3 c3 h_i): linear coefficient of the odd part
+    T h[27];      // h_i = c_i.K~.c_i - cs2 tr K~
+    T Pirest[6];  // sum_i r_i c_ia c_ib = rho0 Theta_ab
+};
+
+// Where the pre-collision population f_i(x, t) of the current state lives:
+//   LOCAL  f_i(x) = A[i][x]                                  (AA pattern, even step count)
+//   PULL   f_i(x) = S[i][x - c_i], or S[opp i][x] if x - c_i is solid   (two-array pull)
+//   AAODD  f_i(x) = A[opp i][x - c_i], or A[i][x] if x - c_i is solid (AA, odd step count)
+enum Layout { LAYOUT_LOCAL = 0, LAYOUT_PULL = 1, LAYOUT_AAODD = 2 };
+
+// Launch shape shared by every per-cell kernel: 256-thread blocks, x fastest.
+struct Shape {
+    dim3 grid, block;
+    long long nblocks;
+};
+Shape shape_for(const Geom& g);
+
+// Kernel launchers of one (lattice, storage) pair. `coef` points at a Coef<double> (storage
+// LBM_FP64) or a Coef<float> (every other storage). Field pointers (rho, u, Pi, f, grad, lam,
+// du0) are double for FP64 and float otherwise; population pointers have the storage type.
+struct Ops {
+    cudaError_t (*init)(const Geom&, const void* coef, int layout, const void* rho, const void* u, void* dst,
+                        cudaStream_t);
+    cudaError_t (*step_pull)(const Geom&, const void* coef, const void* src, void* dst, int* flag, cudaStream_t);
+    cudaError_t (*step_aa)(const Geom&, const void* coef, int odd, const void* src, void* dst, int* flag,
+                           cudaStream_t);
+    cudaError_t (*moments)(const Geom&, const void* coef, int layout, const void* src, void* rho, void* u, void* Pi,
+                           void* f, cudaStream_t);
+    cudaError_t (*totals)(const Geom&, const void* coef, int layout, const void* src, double* partials, int* flag,
+                          cudaStream_t);
+    cudaError_t (*adj_seed)(const Geom&, const void* coef, int layout, const void* src, const void* grad, void* lam,
+                            cudaStream_t);
+    cudaError_t (*adj_step)(const Geom&, const void* coef, int layout, const void* src, const void* lam_next,
+                            void* lam, double* gpart, cudaStream_t);
+    cudaError_t (*adj_init)(const Geom&, const void* coef, const void* rho0, const void* u0, const void* lam0,
+                            void* du0, double* gpart, cudaStream_t);
+};
+
+// One translation unit per (lattice, storage): lbm_ops.cu compiled with LBM_Q / LBM_S.
+#define LBM_OPS_DECL(Q, S) const Ops& ops_q##Q##_s##S();
+LBM_OPS_DECL(9, 0) LBM_OPS_DECL(9, 1) LBM_OPS_DECL(9, 2) LBM_OPS_DECL(9, 3)
+LBM_OPS_DECL(19, 0) LBM_OPS_DECL(19, 1) LBM_OPS_DECL(19, 2) LBM_OPS_DECL(19, 3)
+LBM_OPS_DECL(27, 0) LBM_OPS_DECL(27, 1) LBM_OPS_DECL(27, 2) LBM_OPS_DECL(27, 3)
+#undef LBM_OPS_DECL
+
+// Deterministic FP64 sum of `nb` partial records of `width` doubles into out[width]
+// (one block, fixed order).
+cudaError_t reduce_partials(const double* partials, long long nb, int width, double* out, cudaStream_t s);
+
+}  // namespace lbm

@@ -1,0 +1,841 @@
+// Device code of the anisotropic-equilibrium BGK lattice Boltzmann library (sm_103a).
+//
+// Every kernel runs one thread per lattice cell, x fastest, so that each direction's loads and
+// stores of a warp touch 32 consecutive elements of one structure-of-arrays plane [q][N]
+// (coalesced; the x-1/x+1 shifted reads of a warp straddle one extra 32-byte sector that the
+// neighbouring warp reads anyway, and the y/z-shifted rows are re-read from L2).
+//
+// Arithmetic is carried in the shifted variables d_i = f_i - r_i with r_i the rest equilibrium
+// feq_i(rho0, 0; Theta), whatever the storage form: this keeps the FP32 sums of the moments and
+// of the relaxation on O(u) quantities instead of O(w_i).
+//
+// Equilibrium (Eq. 3rd_order_equilibrium with Eq. feq_i; cs2 = 1/3; K~ = Theta - cs2 I):
+//   feq_i - r_i = E_i + O_i, evaluated once per opposite pair (i, opp i):
+//   even  E_i = drho w_i (1 + 9/2 h_i) + 9/2 rho w_i ((u.c_i)^2 - |u|^2/3)          (= E_opp)
+//   odd   O_i = rho [u.c_i w_i (3 + 3 c3 h_i) + w_i c3 ((u.c_i)^3 - |u|^2 u.c_i - 2 c_i.K~.u)]
+//                                                                                   (= -O_opp)
+//   with drho = rho - rho0, c3 = 9/2 (third order) or 0 (second order).
+// BGK relaxation (Eq. LBE_BGK): d_i <- d_i + (feq_i - r_i - d_i)/tau.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm_internal.h"
+#include "lbm_lattice.cuh"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------------------------
+// Storage forms: 0 FP32 (f), 1 FP64 (f), 2 FP32 shifted (f - r), 3 FP16 shifted (f - r).
+// ---------------------------------------------------------------------------------------------
+template <int S>
+struct Store;
+template <>
+struct Store<0> {
+    using type = float;
+    using T = float;
+    static constexpr bool shifted = false;
+};
+template <>
+struct Store<1> {
+    using type = double;
+    using T = double;
+    static constexpr bool shifted = false;
+};
+template <>
+struct Store<2> {
+    using type = float;
+    using T = float;
+    static constexpr bool shifted = true;
+};
+template <>
+struct Store<3> {
+    using type = __half;
+    using T = float;
+    static constexpr bool shifted = true;
+};
+
+__device__ __forceinline__ float raw_to_T(float v) { return v; }
+__device__ __forceinline__ double raw_to_T(double v) { return v; }
+
+// read-only (non-coherent) loads: used when the source array is not written by the kernel
+__device__ __forceinline__ float ld_ro(const float* p) { return __ldg(p); }
+__device__ __forceinline__ double ld_ro(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ld_ro(const __half* p) {
+    return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p))));
+}
+// coherent loads: used by the in-place AA kernels
+__device__ __forceinline__ float ld_rw(const float* p) { return *p; }
+__device__ __forceinline__ double ld_rw(const double* p) { return *p; }
+__device__ __forceinline__ float ld_rw(const __half* p) {
+    return __half2float(__ushort_as_half(*reinterpret_cast<const unsigned short*>(p)));
+}
+__device__ __forceinline__ void st_raw(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st_raw(double* p, double v) { *p = v; }
+__device__ __forceinline__ void st_raw(__half* p, float v) { *p = __float2half_rn(v); }
+
+template <int S>
+__device__ __forceinline__ typename Store<S>::T to_shifted(typename Store<S>::T raw, typename Store<S>::T r) {
+    return Store<S>::shifted ? raw : raw - r;
+}
+template <int S>
+__device__ __forceinline__ typename Store<S>::T from_shifted(typename Store<S>::T d, typename Store<S>::T r) {
+    return Store<S>::shifted ? d : d + r;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Cell addressing with periodic wrap. X[k] = x - (k - 1) and RW[ky][kz] = (y - (ky - 1)) +
+// ny (z - (kz - 1)), all wrapped, so the index of x - c is X[c.x + 1] + nx RW[c.y + 1][c.z + 1]
+// and the index of x + c is X[1 - c.x] + nx RW[1 - c.y][1 - c.z].
+// ---------------------------------------------------------------------------------------------
+struct Cell {
+    int x, y, z;
+    long long n;
+    int X[3];
+    long long RW[3][3];
+};
+
+__device__ __forceinline__ bool make_cell(const Geom& g, Cell& c) {
+    c.x = blockIdx.x * blockDim.x + threadIdx.x;
+    c.y = blockIdx.y * blockDim.y + threadIdx.y;
+    c.z = blockIdx.z;
+    if (c.x >= g.nx || c.y >= g.ny) return false;
+    const int yy[3] = {c.y + 1 == g.ny ? 0 : c.y + 1, c.y, c.y == 0 ? g.ny - 1 : c.y - 1};
+    const int zz[3] = {c.z + 1 == g.nz ? 0 : c.z + 1, c.z, c.z == 0 ? g.nz - 1 : c.z - 1};
+    c.X[0] = c.x + 1 == g.nx ? 0 : c.x + 1;
+    c.X[1] = c.x;
+    c.X[2] = c.x == 0 ? g.nx - 1 : c.x - 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) c.RW[a][b] = (long long)yy[a] + (long long)g.ny * zz[b];
+    c.n = (long long)c.x + (long long)g.nx * c.RW[1][1];
+    return true;
+}
+
+__device__ __forceinline__ long long idx_minus(const Geom& g, const Cell& c, Vec3 v) {
+    return (long long)c.X[v.x + 1] + (long long)g.nx * c.RW[v.y + 1][v.z + 1];
+}
+__device__ __forceinline__ long long idx_plus(const Geom& g, const Cell& c, Vec3 v) {
+    return (long long)c.X[1 - v.x] + (long long)g.nx * c.RW[1 - v.y][1 - v.z];
+}
+__device__ __forceinline__ bool solid_bit(const Geom& g, int xx, long long row) {
+    return (__ldg(g.mask + row * g.W + (xx >> 5)) >> (xx & 31)) & 1u;
+}
+__device__ __forceinline__ bool solid_minus(const Geom& g, const Cell& c, Vec3 v) {
+    return solid_bit(g, c.X[v.x + 1], c.RW[v.y + 1][v.z + 1]);
+}
+__device__ __forceinline__ bool solid_plus(const Geom& g, const Cell& c, Vec3 v) {
+    return solid_bit(g, c.X[1 - v.x], c.RW[1 - v.y][1 - v.z]);
+}
+__device__ __forceinline__ bool solid_self(const Geom& g, const Cell& c) { return solid_bit(g, c.x, c.RW[1][1]); }
+
+// Gather of the pre-collision populations of one cell in shifted form (see Layout).
+template <int Q, int S, bool MASK, int LAYOUT, bool RO>
+__device__ __forceinline__ void gather(const Geom& g, const Cell& c, const Coef<typename Store<S>::T>& cf,
+                                       const typename Store<S>::type* src, typename Store<S>::T (&d)[Q]) {
+    const long long N = g.N;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const Vec3 v = vel<Q>(i);
+        long long at;
+        if (LAYOUT == LAYOUT_LOCAL || i == 0) {
+            at = (long long)i * N + c.n;
+        } else {
+            const bool wall = MASK && solid_minus(g, c, v);
+            const int slot_n = LAYOUT == LAYOUT_PULL ? i : opp(i);   // slot read from the neighbour
+            const int slot_w = LAYOUT == LAYOUT_PULL ? opp(i) : i;   // slot read on a wall link
+            at = wall ? (long long)slot_w * N + c.n : (long long)slot_n * N + idx_minus(g, c, v);
+        }
+        const auto raw = RO ? ld_ro(src + at) : ld_rw(src + at);
+        d[i] = to_shifted<S>(raw, cf.r[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Moments and equilibrium
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct Macro {
+    T drho, rho, ux, uy, uz;
+};
+
+template <int Q, typename T>
+__device__ __forceinline__ Macro<T> macro_of(const T (&d)[Q], T rho0) {
+    constexpr int P = Lat<Q>::P;
+    T s = d[0], jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        const Vec3 v = vel<Q>(2 * k + 1);
+        const T a = d[2 * k + 1], b = d[2 * k + 2];
+        s += a + b;
+        const T df = a - b;
+        if (v.x == 1) jx += df;
+        if (v.x == -1) jx -= df;
+        if (v.y == 1) jy += df;
+        if (v.y == -1) jy -= df;
+        if (v.z == 1) jz += df;
+        if (v.z == -1) jz -= df;
+    }
+    Macro<T> m;
+    m.drho = s;
+    m.rho = rho0 + s;
+    const T inv = T(1) / m.rho;
+    m.ux = jx * inv;
+    m.uy = jy * inv;
+    m.uz = Lat<Q>::D == 3 ? jz * inv : T(0);
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T dotv(Vec3 v, T ax, T ay, T az) {
+    T r = T(0);
+    if (v.x == 1) r += ax;
+    if (v.x == -1) r -= ax;
+    if (v.y == 1) r += ay;
+    if (v.y == -1) r -= ay;
+    if (v.z == 1) r += az;
+    if (v.z == -1) r -= az;
+    return r;
+}
+
+// Per-cell invariants of the equilibrium.
+template <typename T>
+struct EqCell {
+    T drho, rho, ux, uy, uz, usq, kx, ky, kz, r45;
+};
+
+template <typename T>
+__device__ __forceinline__ EqCell<T> eq_cell(const Coef<T>& cf, T drho, T rho, T ux, T uy, T uz) {
+    EqCell<T> e;
+    e.drho = drho;
+    e.rho = rho;
+    e.ux = ux;
+    e.uy = uy;
+    e.uz = uz;
+    e.usq = ux * ux + uy * uy + uz * uz;
+    e.kx = cf.K[0] * ux + cf.K[3] * uy + cf.K[4] * uz;
+    e.ky = cf.K[3] * ux + cf.K[1] * uy + cf.K[5] * uz;
+    e.kz = cf.K[4] * ux + cf.K[5] * uy + cf.K[2] * uz;
+    e.r45 = T(4.5) * rho;
+    return e;
+}
+
+// Even and odd parts of feq - r for the direction pair (i, opp i), i = 2k + 1.
+template <int Q, typename T>
+__device__ __forceinline__ void pair_eq(const Coef<T>& cf, const EqCell<T>& e, int k, T& E, T& O, T& uc) {
+    const int i = 2 * k + 1;
+    const Vec3 v = vel<Q>(i);
+    const T w = T(weight<Q>(i));
+    uc = dotv<T>(v, e.ux, e.uy, e.uz);
+    const T qk = dotv<T>(v, e.kx, e.ky, e.kz);
+    E = e.drho * cf.A[i] + w * e.r45 * (uc * uc - e.usq * T(1.0 / 3.0));
+    O = e.rho * (uc * cf.B[i] + w * cf.c3 * (uc * (uc * uc - e.usq) - T(2) * qk));
+}
+
+template <int Q, typename T>
+__device__ __forceinline__ T rest_eq(const Coef<T>& cf, const EqCell<T>& e) {
+    return e.drho * cf.A[0] - T(weight<Q>(0)) * e.r45 * e.usq * T(1.0 / 3.0);
+}
+
+// BGK collision in place on shifted populations; returns the macroscopic state.
+template <int Q, typename T>
+__device__ __forceinline__ Macro<T> bgk(const Coef<T>& cf, T (&d)[Q]) {
+    const Macro<T> m = macro_of<Q, T>(d, cf.rho0);
+    const EqCell<T> e = eq_cell<T>(cf, m.drho, m.rho, m.ux, m.uy, m.uz);
+    const T om = cf.omega, om1 = T(1) - cf.omega;
+    d[0] = om1 * d[0] + om * rest_eq<Q, T>(cf, e);
+#pragma unroll
+    for (int k = 0; k < Lat<Q>::P; ++k) {
+        T E, O, uc;
+        pair_eq<Q, T>(cf, e, k, E, O, uc);
+        d[2 * k + 1] = om1 * d[2 * k + 1] + om * (E + O);
+        d[2 * k + 2] = om1 * d[2 * k + 2] + om * (E - O);
+    }
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ bool bad_cell(const Macro<T>& m) {
+    return !(m.rho > T(0)) || !isfinite(m.ux + m.uy + m.uz);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Fused stream + collide, two arrays, pull form: gather f(t) from the post-collision array of
+// the previous step, relax, store at the own cell. One launch per time step.
+// ---------------------------------------------------------------------------------------------
+template <int Q, int S, bool MASK>
+__global__ void __launch_bounds__(256) k_step_pull(Geom g, Coef<typename Store<S>::T> cf,
+                                                   const typename Store<S>::type* __restrict__ src,
+                                                   typename Store<S>::type* __restrict__ dst, int* __restrict__ flag) {
+    using T = typename Store<S>::T;
+    Cell c;
+    if (!make_cell(g, c)) return;
+    if (MASK && solid_self(g, c)) return;
+    T d[Q];
+    gather<Q, S, MASK, LAYOUT_PULL, true>(g, c, cf, src, d);
+    const Macro<T> m = bgk<Q, T>(cf, d);
+    if (bad_cell(m)) *flag = 1;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st_raw(dst + (long long)i * g.N + c.n, from_shifted<S>(d[i], cf.r[i]));
+}
+
+// ---------------------------------------------------------------------------------------------
+// AA pattern (one array, in place; src == dst allowed).
+//   even: read A[i][x], write f*_i to A[opp i][x]                     (state LOCAL -> AAODD)
+//   odd:  read f_i per AAODD, write f*_i to A[i][x + c_i], or to A[opp i][x] if x + c_i is
+//         solid                                                         (state AAODD -> LOCAL)
+// Each thread writes exactly the slots it read, so the in-place update is race free.
+// ---------------------------------------------------------------------------------------------
+template <int Q, int S, bool MASK, int ODD>
+__global__ void __launch_bounds__(256) k_step_aa(Geom g, Coef<typename Store<S>::T> cf,
+                                                 const typename Store<S>::type* src, typename Store<S>::type* dst,
+                                                 int* __restrict__ flag) {
+    using T = typename Store<S>::T;
+    Cell c;
+    if (!make_cell(g, c)) return;
+    if (MASK && solid_self(g, c)) return;
+    T d[Q];
+    if (ODD)
+        gather<Q, S, MASK, LAYOUT_AAODD, false>(g, c, cf, src, d);
+    else
+        gather<Q, S, MASK, LAYOUT_LOCAL, false>(g, c, cf, src, d);
+    const Macro<T> m = bgk<Q, T>(cf, d);
+    if (bad_cell(m)) *flag = 1;
+    const long long N = g.N;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        long long at;
+        if (i == 0) {
+            at = c.n;
+        } else if (!ODD) {
+            at = (long long)opp(i) * N + c.n;
+        } else {
+            const Vec3 v = vel<Q>(i);
+            const bool wall = MASK && solid_plus(g, c, v);
+            at = wall ? (long long)opp(i) * N + c.n : (long long)i * N + idx_plus(g, c, v);
+        }
+        st_raw(dst + at, from_shifted<S>(d[i], cf.r[i]));
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Initial state f(0) = feq(rho, u), written so that the chosen layout gathers it back.
+// ---------------------------------------------------------------------------------------------
+template <int Q, int S, bool MASK, int LAYOUT>
+__global__ void __launch_bounds__(256) k_init(Geom g, Coef<typename Store<S>::T> cf,
+                                              const typename Store<S>::T* __restrict__ rho_in,
+                                              const typename Store<S>::T* __restrict__ u_in,
+                                              typename Store<S>::type* __restrict__ dst) {
+    using T = typename Store<S>::T;
+    Cell c;
+    if (!make_cell(g, c)) return;
+    if (MASK && solid_self(g, c)) return;
+    const long long N = g.N;
+    const T rho = rho_in ? rho_in[c.n] : cf.rho0;
+    const T ux = u_in ? u_in[c.n] : T(0);
+    const T uy = u_in ? u_in[N + c.n] : T(0);
+    const T uz = (u_in && Lat<Q>::D == 3) ? u_in[2 * N + c.n] : T(0);
+    const EqCell<T> e = eq_cell<T>(cf, rho - cf.rho0, rho, ux, uy, uz);
+    T d[Q];
+    d[0] = rest_eq<Q, T>(cf, e);
+#pragma unroll
+    for (int k = 0; k < Lat<Q>::P; ++k) {
+        T E, O, uc;
+        pair_eq<Q, T>(cf, e, k, E, O, uc);
+        d[2 * k + 1] = E + O;
+        d[2 * k + 2] = E - O;
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        long long at;
+        if (LAYOUT == LAYOUT_LOCAL || i == 0) {
+            at = (long long)i * N + c.n;
+        } else {
+            // the slot the PULL gather reads f_i(x) from
+            const Vec3 v = vel<Q>(i);
+            const bool wall = MASK && solid_minus(g, c, v);
+            at = wall ? (long long)opp(i) * N + c.n : (long long)i * N + idx_minus(g, c, v);
+        }
+        st_raw(dst + at, from_shifted<S>(d[i], cf.r[i]));
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Observables of f(t): rho, u, Pi (Eqs. a0discrete_f, a1discrete_f; Appendix E second moment),
+// and optionally the unshifted populations f_i in direction order.
+// ---------------------------------------------------------------------------------------------
+template <int D>
+struct PiIdx;
+template <>
+struct PiIdx<2> {
+    static constexpr int n = 3;
+};
+template <>
+struct PiIdx<3> {
+    static constexpr int n = 6;
+};
+__host__ __device__ constexpr int pi_a(int D, int k) { return D == 2 ? (k == 0 ? 0 : k == 1 ? 1 : 0) : (k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 2 : k == 3 ? 0 : k == 4 ? 0 : 1); }
+__host__ __device__ constexpr int pi_b(int D, int k) { return D == 2 ? (k == 0 ? 0 : k == 1 ? 1 : 1) : (k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 2 : k == 3 ? 1 : k == 4 ? 2 : 2); }
+__host__ __device__ constexpr int pi_full(int D, int k) { return D == 2 ? (k == 2 ? 3 : k) : k; }  // index into K[6]-style xx,yy,zz,xy,xz,yz
+__host__ __device__ constexpr int comp(Vec3 v, int a) { return a == 0 ? v.x : a == 1 ? v.y : v.z; }
+
+template <int Q, int S, bool MASK, int LAYOUT>
+__global__ void __launch_bounds__(256) k_moments(Geom g, Coef<typename Store<S>::T> cf,
+                                                 const typename Store<S>::type* __restrict__ src,
+                                                 typename Store<S>::T* __restrict__ rho_out,
+                                                 typename Store<S>::T* __restrict__ u_out,
+                                                 typename Store<S>::T* __restrict__ pi_out,
+                                                 typename Store<S>::T* __restrict__ f_out) {
+    using T = typename Store<S>::T;
+    constexpr int D = Lat<Q>::D;
+    Cell c;
+    if (!make_cell(g, c)) return;
+    const long long N = g.N;
+    if (MASK && solid_self(g, c)) {
+        if (rho_out) rho_out[c.n] = T(0);
+        if (u_out)
+            for (int a = 0; a < D; ++a) u_out[a * N + c.n] = T(0);
+        if (pi_out)
+            for (int k = 0; k < PiIdx<D>::n; ++k) pi_out[k * N + c.n] = T(0);
+        if (f_out)
+            for (int i = 0; i < Q; ++i) f_out[i * N + c.n] = T(0);
+        return;
+    }
+    T d[Q];
+    gather<Q, S, MASK, LAYOUT, true>(g, c, cf, src, d);
+    const Macro<T> m = macro_of<Q, T>(d, cf.rho0);
+    if (rho_out) rho_out[c.n] = m.rho;
+    if (u_out) {
+        u_out[c.n] = m.ux;
+        u_out[N + c.n] = m.uy;
+        if (D == 3) u_out[2 * N + c.n] = m.uz;
+    }
+    if (pi_out) {
+#pragma unroll
+        for (int k = 0; k < PiIdx<D>::n; ++k) {
+            T s = T(0);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const int p = comp(vel<Q>(i), pi_a(D, k)) * comp(vel<Q>(i), pi_b(D, k));
+                if (p == 1) s += d[i];
+                if (p == -1) s -= d[i];
+            }
+            pi_out[k * N + c.n] = cf.Pirest[pi_full(D, k)] + s;
+        }
+    }
+    if (f_out) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f_out[i * N + c.n] = d[i] + cf.r[i];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Block-level FP64 reduction of W values per thread into rec[W] (thread 0 holds the result).
+// ---------------------------------------------------------------------------------------------
+template <int W>
+__device__ __forceinline__ void block_sum(double (&v)[W], double (&out)[W]) {
+    __shared__ double sh[8][W];
+    const int lane = (threadIdx.x + threadIdx.y * blockDim.x) & 31;
+    const int warp = (threadIdx.x + threadIdx.y * blockDim.x) >> 5;
+    const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        double s = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        v[k] = s;
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < W; ++k) sh[warp][k] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            double s = lane < nwarps ? sh[lane][k] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            out[k] = s;
+        }
+    }
+}
+
+__device__ __forceinline__ long long block_linear() {
+    return (long long)blockIdx.x + (long long)gridDim.x * ((long long)blockIdx.y + (long long)gridDim.y * blockIdx.z);
+}
+
+// Totals over fluid cells: partial[block][0] = sum rho, [1..3] = sum j, in FP64.
+template <int Q, int S, bool MASK, int LAYOUT>
+__global__ void __launch_bounds__(256) k_totals(Geom g, Coef<typename Store<S>::T> cf,
+                                                const typename Store<S>::type* __restrict__ src,
+                                                double* __restrict__ partials, int* __restrict__ flag) {
+    using T = typename Store<S>::T;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    Cell c;
+    if (make_cell(g, c) && !(MASK && solid_self(g, c))) {
+        T d[Q];
+        gather<Q, S, MASK, LAYOUT, true>(g, c, cf, src, d);
+        const Macro<T> m = macro_of<Q, T>(d, cf.rho0);
+        if (bad_cell(m)) *flag = 1;
+        v[0] = (double)m.rho;
+        v[1] = (double)m.rho * (double)m.ux;
+        v[2] = (double)m.rho * (double)m.uy;
+        v[3] = (double)m.rho * (double)m.uz;
+    }
+    double out[4];
+    block_sum<4>(v, out);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const long long b = block_linear();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) partials[b * 4 + k] = out[k];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Discrete adjoint. lambda_t,i(x) = dL/df_i(x, t) for the pre-collision state, plain [q][N].
+//   seed   lambda_T,i = sum_a g_a (c_ia - u_a) / rho                               (du/df)
+//   step   mu_i(x) = lambda_{t+1,i}(x + c_i), or lambda_{t+1,opp i}(x) if x + c_i is solid
+//          (transpose of streaming with bounce-back), then
+//          lambda_t,i = (1 - 1/tau) mu_i + (1/tau) (v0 + c_i . v)                 (J_C^T mu)
+//          with v0 = sum_i mu_i dfeq_i/drho |_j and v = sum_i mu_i dfeq_i/dj.
+//   params dL/dtau  += -(1/tau^2) sum_i mu_i (feq_i - f_i)
+//          dL/dK~ab += (1/tau) sum_i mu_i dfeq_i/dK~ab (and once more at t = 0 through f(0) =
+//          feq(rho0, u0), without the 1/tau).
+// With feq_i = w_i rho P_i(u), u = j/rho, and P_i the bracket of the equilibrium:
+//   dP_i/du = c_i (3 + 9 uc + c3 (3 uc^2 - |u|^2 + 3 h_i)) - u (3 + 2 c3 uc) - 2 c3 K~ c_i
+//   P_i - u.dP_i/du = 1 + 9/2 h_i - 9/2 uc^2 + 3/2 |u|^2 - 2 c3 uc (uc^2 - |u|^2)
+//   dfeq_i/dK~ab = w_i rho [9/2 (c_a c_b - d_ab/3) + c3 (3 uc (c_a c_b - d_ab/3) - 2 c_a u_b)]
+// The per-pair sums below use mu_i + mu_opp (even terms) and mu_i - mu_opp (odd terms).
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct AdjAcc {
+    T v0, B, P0, Q0;
+    T Va[3], V[3];
+    T P[6], Qm[6];  // xx yy zz xy xz yz
+};
+
+template <int Q, typename T>
+__device__ __forceinline__ AdjAcc<T> adj_accumulate(const Coef<T>& cf, const EqCell<T>& e, const T (&mu)[Q],
+                                                    T* gtau_part, const T* d) {
+    AdjAcc<T> A;
+    A.v0 = A.B = A.P0 = A.Q0 = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) A.Va[a] = A.V[a] = T(0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) A.P[k] = A.Qm[k] = T(0);
+    const T usq = e.usq;
+    const T c3 = cf.c3;
+    {  // rest direction
+        const T w = T(weight<Q>(0));
+        const T m = w * mu[0];
+        A.P0 += m;
+        A.B += T(3) * m;
+        A.v0 += m * (T(1) + T(4.5) * cf.h[0] + T(1.5) * usq);
+        if (gtau_part) *gtau_part += mu[0] * (rest_eq<Q, T>(cf, e) - d[0]);
+    }
+#pragma unroll
+    for (int k = 0; k < Lat<Q>::P; ++k) {
+        const int i = 2 * k + 1;
+        const Vec3 v = vel<Q>(i);
+        const T w = T(weight<Q>(i));
+        T E, O, uc;
+        pair_eq<Q, T>(cf, e, k, E, O, uc);
+        const T sm = w * (mu[i] + mu[i + 1]);
+        const T dm = w * (mu[i] - mu[i + 1]);
+        const T uc2 = uc * uc;
+        A.P0 += sm;
+        A.Q0 += uc * dm;
+        A.B += T(3) * sm + T(2) * c3 * uc * dm;
+        A.v0 += sm * (T(1) + T(4.5) * cf.h[i] - T(4.5) * uc2 + T(1.5) * usq) - T(2) * c3 * uc * (uc2 - usq) * dm;
+        const T al = (T(3) + c3 * (T(3) * uc2 - usq + T(3) * cf.h[i])) * dm + T(9) * uc * sm;
+        const T cc[3] = {T(v.x), T(v.y), T(v.z)};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (comp(v, a) != 0) {
+                A.Va[a] += cc[a] * al;
+                A.V[a] += cc[a] * dm;
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+            const int ca = comp(v, p < 3 ? p : (p == 5 ? 1 : 0));
+            const int cb = comp(v, p < 3 ? p : (p == 3 ? 1 : 2));
+            const int s = ca * cb;
+            if (s == 1) {
+                A.P[p] += sm;
+                A.Qm[p] += uc * dm;
+            } else if (s == -1) {
+                A.P[p] -= sm;
+                A.Qm[p] -= uc * dm;
+            }
+        }
+        if (gtau_part) *gtau_part += mu[i] * (E + O - d[i]) + mu[i + 1] * (E - O - d[i + 1]);
+    }
+    return A;
+}
+
+// v = dfeq/dj contracted with mu; G = symmetric Theta-gradient contribution (without 1/tau).
+template <int Q, typename T>
+__device__ __forceinline__ void adj_finish(const Coef<T>& cf, const EqCell<T>& e, const AdjAcc<T>& A, T (&v)[3],
+                                           T (&G)[6]) {
+    const T u[3] = {e.ux, e.uy, e.uz};
+    const T c3 = cf.c3;
+    const T KV[3] = {cf.K[0] * A.V[0] + cf.K[3] * A.V[1] + cf.K[4] * A.V[2],
+                     cf.K[3] * A.V[0] + cf.K[1] * A.V[1] + cf.K[5] * A.V[2],
+                     cf.K[4] * A.V[0] + cf.K[5] * A.V[1] + cf.K[2] * A.V[2]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[a] = A.Va[a] - u[a] * A.B - T(2) * c3 * KV[a];
+    const T rho = e.rho;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        G[a] = rho * (T(4.5) * (A.P[a] - A.P0 * T(1.0 / 3.0)) +
+                      c3 * (T(3) * (A.Qm[a] - A.Q0 * T(1.0 / 3.0)) - T(2) * A.V[a] * u[a]));
+    // off-diagonal: dL/dTheta_ab + dL/dTheta_ba
+    G[3] = rho * (T(9) * A.P[3] + c3 * (T(6) * A.Qm[3] - T(2) * (A.V[0] * u[1] + A.V[1] * u[0])));
+    G[4] = rho * (T(9) * A.P[4] + c3 * (T(6) * A.Qm[4] - T(2) * (A.V[0] * u[2] + A.V[2] * u[0])));
+    G[5] = rho * (T(9) * A.P[5] + c3 * (T(6) * A.Qm[5] - T(2) * (A.V[1] * u[2] + A.V[2] * u[1])));
+}
+
+// Gradient record per block: [0..5] Theta (xx yy zz xy xz yz), [6] tau, [7] unused.
+__device__ __forceinline__ void accumulate_record(double (&v)[8], double* gpart) {
+    double out[8];
+    block_sum<8>(v, out);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const long long b = block_linear();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) gpart[b * 8 + k] += out[k];
+    }
+}
+
+template <int Q, int S, bool MASK, int LAYOUT>
+__global__ void __launch_bounds__(256) k_adj_seed(Geom g, Coef<typename Store<S>::T> cf,
+                                                  const typename Store<S>::type* __restrict__ src,
+                                                  const typename Store<S>::T* __restrict__ grad,
+                                                  typename Store<S>::T* __restrict__ lam) {
+    using T = typename Store<S>::T;
+    Cell c;
+    if (!make_cell(g, c)) return;
+    if (MASK && solid_self(g, c)) return;
+    const long long N = g.N;
+    T d[Q];
+    gather<Q, S, MASK, LAYOUT, true>(g, c, cf, src, d);
+    const Macro<T> m = macro_of<Q, T>(d, cf.rho0);
+    const T gx = grad[c.n], gy = grad[N + c.n], gz = Lat<Q>::D == 3 ? grad[2 * N + c.n] : T(0);
+    const T inv = T(1) / m.rho;
+    const T gu = gx * m.ux + gy * m.uy + gz * m.uz;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) lam[i * N + c.n] = (dotv<T>(vel<Q>(i), gx, gy, gz) - gu) * inv;
+}
+
+template <int Q, int S, bool MASK, int LAYOUT>
+__global__ void __launch_bounds__(256) k_adj_step(Geom g, Coef<typename Store<S>::T> cf,
+                                                  const typename Store<S>::type* __restrict__ src,
+                                                  const typename Store<S>::T* __restrict__ lam_next,
+                                                  typename Store<S>::T* __restrict__ lam, double* __restrict__ gpart) {
+    using T = typename Store<S>::T;
+    double rec[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    Cell c;
+    if (make_cell(g, c) && !(MASK && solid_self(g, c))) {
+        const long long N = g.N;
+        T d[Q];
+        gather<Q, S, MASK, LAYOUT, true>(g, c, cf, src, d);
+        T mu[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (i == 0) {
+                mu[0] = lam_next[c.n];
+            } else {
+                const Vec3 v = vel<Q>(i);
+                const bool wall = MASK && solid_plus(g, c, v);
+                mu[i] = wall ? lam_next[(long long)opp(i) * N + c.n] : lam_next[(long long)i * N + idx_plus(g, c, v)];
+            }
+        }
+        const Macro<T> m = macro_of<Q, T>(d, cf.rho0);
+        const EqCell<T> e = eq_cell<T>(cf, m.drho, m.rho, m.ux, m.uy, m.uz);
+        T gt = T(0);
+        const AdjAcc<T> A = adj_accumulate<Q, T>(cf, e, mu, &gt, d);
+        T v[3], G[6];
+        adj_finish<Q, T>(cf, e, A, v, G);
+        const T om = cf.omega, om1 = T(1) - cf.omega;
+        lam[c.n] = om1 * mu[0] + om * A.v0;
+#pragma unroll
+        for (int k = 0; k < Lat<Q>::P; ++k) {
+            const int i = 2 * k + 1;
+            const T cv = dotv<T>(vel<Q>(i), v[0], v[1], v[2]);
+            lam[(long long)i * N + c.n] = om1 * mu[i] + om * (A.v0 + cv);
+            lam[(long long)(i + 1) * N + c.n] = om1 * mu[i + 1] + om * (A.v0 - cv);
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) rec[k] = (double)(om * G[k]);
+        rec[6] = -(double)(om * om) * (double)gt;
+    }
+    accumulate_record(rec, gpart);
+}
+
+template <int Q, typename T>
+__global__ void __launch_bounds__(256) k_adj_init(Geom g, Coef<T> cf, const T* __restrict__ rho0,
+                                                  const T* __restrict__ u0, const T* __restrict__ lam0,
+                                                  T* __restrict__ du0, double* __restrict__ gpart) {
+    double rec[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    Cell c;
+    const bool live = make_cell(g, c);
+    if (live) {
+        const long long N = g.N;
+        const bool solid = g.mask && solid_self(g, c);
+        if (solid) {
+            if (du0)
+                for (int a = 0; a < Lat<Q>::D; ++a) du0[a * N + c.n] = T(0);
+        } else {
+            const T rho = rho0 ? rho0[c.n] : cf.rho0;
+            const T ux = u0 ? u0[c.n] : T(0), uy = u0 ? u0[N + c.n] : T(0);
+            const T uz = (u0 && Lat<Q>::D == 3) ? u0[2 * N + c.n] : T(0);
+            const EqCell<T> e = eq_cell<T>(cf, rho - cf.rho0, rho, ux, uy, uz);
+            T mu[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) mu[i] = lam0[(long long)i * N + c.n];
+            const AdjAcc<T> A = adj_accumulate<Q, T>(cf, e, mu, nullptr, nullptr);
+            T v[3], G[6];
+            adj_finish<Q, T>(cf, e, A, v, G);
+            if (du0)
+                for (int a = 0; a < Lat<Q>::D; ++a) du0[a * N + c.n] = rho * v[a];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) rec[k] = (double)G[k];
+        }
+    }
+    accumulate_record(rec, gpart);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host-side launchers of one (lattice, storage) pair, dispatching over mask and layout.
+// ---------------------------------------------------------------------------------------------
+template <int Q, int S>
+struct Launch {
+    using ST = typename Store<S>::type;
+    using T = typename Store<S>::T;
+    using CF = Coef<T>;
+
+    static cudaError_t init(const Geom& g, const void* coef, int layout, const void* rho, const void* u, void* dst,
+                            cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        auto r = static_cast<const T*>(rho);
+        auto uu = static_cast<const T*>(u);
+        auto o = static_cast<ST*>(dst);
+        const bool m = g.mask != nullptr;
+        if (layout == LAYOUT_PULL) {
+            if (m)
+                k_init<Q, S, true, LAYOUT_PULL><<<sh.grid, sh.block, 0, st>>>(g, cf, r, uu, o);
+            else
+                k_init<Q, S, false, LAYOUT_PULL><<<sh.grid, sh.block, 0, st>>>(g, cf, r, uu, o);
+        } else {
+            if (m)
+                k_init<Q, S, true, LAYOUT_LOCAL><<<sh.grid, sh.block, 0, st>>>(g, cf, r, uu, o);
+            else
+                k_init<Q, S, false, LAYOUT_LOCAL><<<sh.grid, sh.block, 0, st>>>(g, cf, r, uu, o);
+        }
+        return cudaGetLastError();
+    }
+
+    static cudaError_t step_pull(const Geom& g, const void* coef, const void* src, void* dst, int* flag,
+                                 cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        auto a = static_cast<const ST*>(src);
+        auto b = static_cast<ST*>(dst);
+        if (g.mask)
+            k_step_pull<Q, S, true><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
+        else
+            k_step_pull<Q, S, false><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t step_aa(const Geom& g, const void* coef, int odd, const void* src, void* dst, int* flag,
+                               cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        auto a = static_cast<const ST*>(src);
+        auto b = static_cast<ST*>(dst);
+        if (g.mask) {
+            if (odd)
+                k_step_aa<Q, S, true, 1><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
+            else
+                k_step_aa<Q, S, true, 0><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
+        } else {
+            if (odd)
+                k_step_aa<Q, S, false, 1><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
+            else
+                k_step_aa<Q, S, false, 0><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
+        }
+        return cudaGetLastError();
+    }
+
+// Expands to the three layouts times mask / no mask for a kernel template K<Q, S, MASK, LAYOUT>.
+#define LBM_BY_LAYOUT(K, ...)                                                                      \
+    do {                                                                                           \
+        const bool m_ = g.mask != nullptr;                                                         \
+        if (layout == LAYOUT_PULL) {                                                               \
+            if (m_) K<Q, S, true, LAYOUT_PULL><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);         \
+            else K<Q, S, false, LAYOUT_PULL><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);           \
+        } else if (layout == LAYOUT_AAODD) {                                                       \
+            if (m_) K<Q, S, true, LAYOUT_AAODD><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);        \
+            else K<Q, S, false, LAYOUT_AAODD><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);          \
+        } else {                                                                                   \
+            if (m_) K<Q, S, true, LAYOUT_LOCAL><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);        \
+            else K<Q, S, false, LAYOUT_LOCAL><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);          \
+        }                                                                                          \
+    } while (0)
+
+    static cudaError_t moments(const Geom& g, const void* coef, int layout, const void* src, void* rho, void* u,
+                               void* Pi, void* f, cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        LBM_BY_LAYOUT(k_moments, g, cf, static_cast<const ST*>(src), static_cast<T*>(rho), static_cast<T*>(u),
+                      static_cast<T*>(Pi), static_cast<T*>(f));
+        return cudaGetLastError();
+    }
+
+    static cudaError_t totals(const Geom& g, const void* coef, int layout, const void* src, double* part, int* flag,
+                              cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        LBM_BY_LAYOUT(k_totals, g, cf, static_cast<const ST*>(src), part, flag);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t adj_seed(const Geom& g, const void* coef, int layout, const void* src, const void* grad,
+                                void* lam, cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        LBM_BY_LAYOUT(k_adj_seed, g, cf, static_cast<const ST*>(src), static_cast<const T*>(grad),
+                      static_cast<T*>(lam));
+        return cudaGetLastError();
+    }
+
+    static cudaError_t adj_step(const Geom& g, const void* coef, int layout, const void* src, const void* lam_next,
+                                void* lam, double* gpart, cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        LBM_BY_LAYOUT(k_adj_step, g, cf, static_cast<const ST*>(src), static_cast<const T*>(lam_next),
+                      static_cast<T*>(lam), gpart);
+        return cudaGetLastError();
+    }
+#undef LBM_BY_LAYOUT
+
+    static cudaError_t adj_init(const Geom& g, const void* coef, const void* rho0, const void* u0, const void* lam0,
+                                void* du0, double* gpart, cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        k_adj_init<Q, T><<<sh.grid, sh.block, 0, st>>>(g, cf, static_cast<const T*>(rho0), static_cast<const T*>(u0),
+                                                       static_cast<const T*>(lam0), static_cast<T*>(du0), gpart);
+        return cudaGetLastError();
+    }
+
+    static const Ops& ops() {
+        static const Ops o = {&init, &step_pull, &step_aa, &moments, &totals, &adj_seed, &adj_step, &adj_init};
+        return o;
+    }
+};
+
+}  // namespace lbm

@@ -151,7 +151,7 @@ def noise_field(N: int, d: int, amp: float, seed: int, rho_amp: float = 0.0):
 # Geometry
 # --------------------------------------------------------------------------------------------
 def porous_spheres(nx: int, ny: int, nz: int, rmin: float = 8.0, rmax: float = 16.0, target: float = 0.30,
-                   seed: int = SEED_BASE + 3, walls: bool = True, max_spheres: int = 100000):
+                   seed: int = SEED_BASE + 3, walls: bool = True, max_spheres: int = 1000000):
     """Overlapping-sphere porous medium between solid planes z = 0 and z = nz-1.
 
     Spheres with centres uniform over the box and radii U[rmin, rmax] are added (a cell is solid
@@ -160,22 +160,27 @@ def porous_spheres(nx: int, ny: int, nz: int, rmin: float = 8.0, rmax: float = 1
     """
     rng = np.random.default_rng(seed)
     solid = np.zeros((nz, ny, nx), dtype=bool)
-    zi = np.arange(nz, dtype=np.float64)[:, None, None]
-    yi = np.arange(ny, dtype=np.float64)[None, :, None]
-    xi = np.arange(nx, dtype=np.float64)[None, None, :]
-    interior = slice(1, nz - 1) if walls else slice(0, nz)
-    n_int = (nz - 2 if walls else nz) * ny * nx
+    z_lo, z_hi = (1, nz - 1) if walls else (0, nz)
+    n_int = (z_hi - z_lo) * ny * nx
+    n_solid = 0
     count = 0
-    while solid[interior].sum() < target * n_int and count < max_spheres:
+    while n_solid < target * n_int and count < max_spheres:
         cx, cy, cz = rng.uniform(0, nx), rng.uniform(0, ny), rng.uniform(0, nz)
         r = rng.uniform(rmin, rmax)
-        z0, z1 = max(0, int(math.floor(cz - r))), min(nz, int(math.ceil(cz + r)) + 1)
-        dz2 = (zi[z0:z1] - cz) ** 2
-        dy = np.abs(yi - cy)
-        dy = np.minimum(dy, ny - dy)
-        dx = np.abs(xi - cx)
-        dx = np.minimum(dx, nx - dx)
-        solid[z0:z1] |= (dz2 + dy ** 2 + dx ** 2) <= r * r
+        zs = np.arange(max(0, int(math.floor(cz - r))), min(nz, int(math.ceil(cz + r)) + 1))
+        ys = np.arange(int(math.floor(cy - r)), int(math.ceil(cy + r)) + 1)
+        xs = np.arange(int(math.floor(cx - r)), int(math.ceil(cx + r)) + 1)
+        d2 = ((zs[:, None, None] - cz) ** 2 + (ys[None, :, None] - cy) ** 2 + (xs[None, None, :] - cx) ** 2)
+        inside = d2 <= r * r
+        yw = np.unique(ys % ny, return_index=True)[1]
+        xw = np.unique(xs % nx, return_index=True)[1]
+        inside = inside[:, yw][:, :, xw]
+        zz, yy, xx = zs, ys[yw] % ny, xs[xw] % nx
+        box = solid[np.ix_(zz, yy, xx)]
+        new = inside & ~box
+        zmask = ((zz >= z_lo) & (zz < z_hi))[:, None, None]
+        n_solid += int((new & zmask).sum())
+        solid[np.ix_(zz, yy, xx)] = box | inside
         count += 1
     if walls:
         solid[0] = True

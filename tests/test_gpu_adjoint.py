@@ -1,0 +1,77 @@
+"""GPU discrete adjoint against the oracle's FP64 adjoint (itself pinned by finite differences).
+
+The loss gradient dL/du(T) is a fixed seeded field g, so the adjoint of both sides is the
+gradient of L = sum g.u(T). FP64 storage must agree to 1e-10 relative; FP32 to 1e-3.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_27004_gb300 import inputs
+
+from gpu_util import rand_theta, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2605_27004_gb300 import build
+    build.build()
+
+
+def _run(q, dims, solid, storage, scheme, K, steps, order=3, seed=0):
+    import torch
+    from paper_2605_27004_gb300 import lbm
+    d = oracle.D_OF_Q[q]
+    N = int(np.prod(dims))
+    Th = rand_theta(50 + q + seed, d, 0.03)
+    tau = 0.7
+    rho0, u0 = inputs.noise_field(N, d, 0.04, 60 + q + seed, rho_amp=0.02)
+    rng = np.random.default_rng(70 + q + seed)
+    g = rng.standard_normal((d, N))
+    if solid is not None:
+        u0 = u0 * (1 - solid)[None, :]
+        g = g * (1 - solid)[None, :]
+    L = lbm.LBM(q, *dims, tau, Th, solid=solid, storage=storage, scheme=scheme, order=order)
+    L.init(torch.as_tensor(rho0), torch.as_tensor(u0))
+    L.step(steps)
+    L.adjoint(torch.as_tensor(g), steps, K)
+    dth, dtau, du0 = L.gradients()
+    pb = oracle.Problem(q, *dims, tau, Th, solid=solid, order=order)
+    odth, odtau, odu0 = pb.adjoint(rho0, u0, steps, g)
+    return dth, dtau, du0.double().cpu().numpy(), odth, odtau, odu0
+
+
+@pytest.mark.parametrize("q,dims", [(9, (37, 21, 1)), (19, (21, 12, 9)), (27, (19, 11, 8))])
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+@pytest.mark.parametrize("mask", [False, True])
+@pytest.mark.parametrize("K", [1, 4, 0])
+def test_adjoint_fp64_matches_oracle(q, dims, scheme, mask, K):
+    N = int(np.prod(dims))
+    solid = inputs.random_mask(N, 0.2, 80 + q) if mask else None
+    steps = 11
+    dth, dtau, du0, odth, odtau, odu0 = _run(q, dims, solid, "fp64", scheme, K, steps)
+    assert np.abs(dth - odth).max() <= 1e-10 * np.abs(odth).max()
+    assert abs(dtau - odtau) <= 1e-10 * abs(odtau)
+    assert rel_l2(du0, odu0) < 1e-10
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_adjoint_order2_fp64(order):
+    dth, dtau, du0, odth, odtau, odu0 = _run(19, (16, 10, 7), None, "fp64", "pull", 3, 9, order=order)
+    assert np.abs(dth - odth).max() <= 1e-10 * np.abs(odth).max()
+    assert abs(dtau - odtau) <= 1e-10 * abs(odtau)
+    assert rel_l2(du0, odu0) < 1e-10
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp32s", "fp16s"])
+def test_adjoint_reduced_precision(storage):
+    """FP32 adjoint (FP64 gradient accumulation) against the FP64 oracle adjoint on 24^3, 60 steps."""
+    q, dims = 19, (24, 24, 24)
+    dth, dtau, du0, odth, odtau, odu0 = _run(q, dims, None, storage, "pull", 10, 60)
+    tol = 1e-3 if storage != "fp16s" else 2e-2
+    print(storage, np.abs(dth - odth).max() / np.abs(odth).max(), abs(dtau - odtau) / abs(odtau), rel_l2(du0, odu0))
+    assert np.abs(dth - odth).max() <= tol * np.abs(odth).max()
+    assert abs(dtau - odtau) <= tol * abs(odtau)
+    assert rel_l2(du0, odu0) < tol

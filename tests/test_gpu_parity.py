@@ -1,0 +1,189 @@
+"""GPU parity: the CUDA library against the FP64 oracle on identical seeded inputs.
+
+Every test runs the library through its C ABI (ctypes binding) on cuda:0 and compares element
+by element with the oracle. Sizes span several thread blocks with ragged tails in x and y.
+Tolerances: FP64 storage 1e-12 relative (populations to 1e-13 absolute, values <= 0.5);
+FP32-shifted 1e-5 and FP16-shifted 1e-3 relative velocity L2 after 1000 steps.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_27004_gb300 import inputs
+
+from gpu_util import gpu_run, oracle_run, perm_lib_to_oracle, rand_theta, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2605_27004_gb300 import build
+    build.build()
+
+
+GEOMS = {9: (70, 37, 1), 19: (45, 13, 9), 27: (37, 11, 10)}
+
+
+def _mask(q, dims, kind, seed=5):
+    N = int(np.prod(dims))
+    if kind is None:
+        return None
+    if kind == "random":
+        return inputs.random_mask(N, 0.2, seed)
+    if kind == "walls":
+        nx, ny, nz = dims
+        if q == 9:
+            m = np.zeros((ny, nx), np.uint8)
+            m[0] = 1
+            m[-1] = 1
+            return m.reshape(-1)
+        return inputs.channel_walls(nx, ny, nz)
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("q", [9, 19, 27])
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+@pytest.mark.parametrize("mask", [None, "random", "walls"])
+@pytest.mark.parametrize("order,steps", [(3, 41), (2, 40)])
+def test_fp64_populations_match_oracle(q, scheme, mask, order, steps):
+    dims = GEOMS[q]
+    d = oracle.D_OF_Q[q]
+    N = int(np.prod(dims))
+    Th = rand_theta(10 + q, d)
+    solid = _mask(q, dims, mask)
+    rho0, u0 = inputs.noise_field(N, d, 0.05, 20 + q, rho_amp=0.02)
+    g = gpu_run(q, dims, 0.7, Th, rho0, u0, steps, solid=solid, order=order, storage="fp64", scheme=scheme)
+    o = oracle_run(q, dims, 0.7, Th, rho0, u0, steps, solid=solid, order=order)
+    perm = perm_lib_to_oracle(q)
+    f_or = o["f"][:, perm].T
+    assert np.abs(g["f"] - f_or).max() < 1e-13
+    fl = slice(None) if solid is None else (solid == 0)
+    assert np.abs(g["rho"] - o["rho"]).max() < 1e-13
+    assert rel_l2(g["u"][:, fl], o["u"][:, fl]) < 1e-12
+    assert np.abs(g["Pi"] - o["Pi"]).max() < 1e-13
+    if solid is not None:
+        assert np.all(g["rho"][solid == 1] == 0)
+
+
+def test_config1_shear_wave_fp64():
+    """D2Q9, FP64, 64x64 periodic, tau 0.8, Theta [[0.36,0.02],[0.02,0.30]], u_x = 0.01 sin(2 pi y/64)
+    + 1e-4 noise, 1000 steps: fields, totals and the shear-wave decay rate."""
+    q, dims, tau = 9, (64, 64, 1), 0.8
+    Th = np.array([[0.36, 0.02], [0.02, 0.30]])
+    rho0, u0 = inputs.shear_wave_2d(64, 64, 0.01, 1e-4, seed=inputs.SEED_BASE + 1)
+    g = gpu_run(q, dims, tau, Th, rho0, u0, 1000, storage="fp64")
+    o = oracle_run(q, dims, tau, Th, rho0, u0, 1000)
+    assert rel_l2(g["u"], o["u"]) < 1e-12
+    assert rel_l2(g["rho"], o["rho"]) < 1e-12
+    m_g, p_g = g["ctx"].totals()
+    m_o, p_o = o["pb"].totals(o["f"])
+    assert abs(m_g - m_o) < 1e-12 * m_o
+    assert np.abs(p_g - p_o).max() < 1e-12 * m_o
+    # decay of the sin(2 pi y / 64) projection against the exact linear rate
+    from oracle import linear
+    _, y, _ = inputs._grid(64, 64, 1)
+    s = np.sin(2 * np.pi * y / 64)
+    a0 = (u0[0] * s).sum()
+    a1 = (g["u"][0] * s).sum()
+    rate = -np.log(a1 / a0) / 1000
+    lin = linear.shear_rate(9, Th, tau, [0, 2 * np.pi / 64], [1, 0])
+    assert abs(rate - lin) / lin < 5e-3
+
+
+@pytest.mark.parametrize("storage,tol", [("fp32s", 1e-5), ("fp16s", 1e-3), ("fp32", 1e-4)])
+def test_reduced_precision_taylor_green_d3q19(storage, tol):
+    """D3Q19 Taylor-Green (u0 = 0.02, rotated Theta, tau 0.6), 1000 steps, against the FP64 oracle."""
+    n = 32
+    Th = inputs.theta_rotated([0.36, 0.33, 0.30], inputs.SEED_BASE + 2)
+    rho0, u0 = inputs.taylor_green_3d(n, 0.02)
+    g = gpu_run(19, (n, n, n), 0.6, Th, rho0, u0, 1000, storage=storage)
+    o = oracle_run(19, (n, n, n), 0.6, Th, rho0, u0, 1000)
+    err = rel_l2(g["u"], o["u"])
+    print(f"{storage}: rel u L2 = {err:.3e}")
+    assert err < tol
+
+
+@pytest.mark.parametrize("storage,tol", [("fp32s", 1e-5), ("fp16s", 1e-3)])
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+def test_reduced_precision_porous_d3q27(storage, tol, scheme):
+    """D3Q27 porous medium between walls (config-3 recipe at 40x36x30), u_x = 0.03, 300 steps."""
+    dims = (40, 36, 30)
+    solid = inputs.porous_spheres(*dims, rmin=3, rmax=6, seed=inputs.SEED_BASE + 3)
+    N = int(np.prod(dims))
+    u0 = np.zeros((3, N))
+    u0[0] = 0.03 * (1 - solid)
+    rho0 = np.ones(N)
+    Th = np.diag([0.38, 0.33, 0.29])
+    g = gpu_run(27, dims, 0.7, Th, rho0, u0, 300, solid=solid, storage=storage, scheme=scheme)
+    o = oracle_run(27, dims, 0.7, Th, rho0, u0, 300, solid=solid)
+    fl = solid == 0
+    err = rel_l2(g["u"][:, fl], o["u"][:, fl])
+    print(f"{storage}/{scheme}: rel u L2 = {err:.3e}")
+    assert err < tol
+    m_g, _ = g["ctx"].totals()
+    m_o, _ = o["pb"].totals(o["f"])
+    assert abs(m_g - m_o) / m_o < 10 * tol
+
+
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+def test_graph_replay_is_bit_identical(scheme):
+    q, dims = 19, (33, 17, 12)
+    N = int(np.prod(dims))
+    Th = rand_theta(3, 3)
+    rho0, u0 = inputs.noise_field(N, 3, 0.03, 4)
+    a = gpu_run(q, dims, 0.6, Th, rho0, u0, 37, storage="fp32", scheme=scheme, use_graphs=1)
+    b = gpu_run(q, dims, 0.6, Th, rho0, u0, 37, storage="fp32", scheme=scheme, use_graphs=-1)
+    assert np.array_equal(a["f"], b["f"])
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16s", "fp64"])
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+def test_state_roundtrip_bit_exact(storage, scheme):
+    import torch
+    from paper_2605_27004_gb300 import lbm
+    q, dims = 27, (29, 14, 11)
+    N = int(np.prod(dims))
+    Th = rand_theta(8, 3)
+    solid = inputs.random_mask(N, 0.15, 9)
+    rho0, u0 = inputs.noise_field(N, 3, 0.03, 10)
+    A = lbm.LBM(q, *dims, 0.65, Th, solid=solid, storage=storage, scheme=scheme)
+    A.init(torch.as_tensor(rho0), torch.as_tensor(u0))
+    A.step(13)
+    st = A.get_state()
+    A.step(20)
+    fa = A.populations().cpu()
+    B = lbm.LBM(q, *dims, 0.65, Th, solid=solid, storage=storage, scheme=scheme)
+    B.set_state(st)
+    assert B.steps == 13
+    B.step(20)
+    fb = B.populations().cpu()
+    assert torch.equal(fa, fb)
+
+
+def test_error_paths():
+    import torch
+    from paper_2605_27004_gb300 import lbm
+    q, dims = 19, (16, 8, 8)
+    N = int(np.prod(dims))
+    L = lbm.LBM(q, *dims, 0.7, np.eye(3) / 3)
+    with pytest.raises(lbm.LBMError) as e:
+        L.step(1)
+    assert e.value.status == -9
+    rho0, u0 = inputs.noise_field(N, 3, 0.01, 1)
+    L.init(torch.as_tensor(rho0), torch.as_tensor(u0))
+    L.step(3)
+    with pytest.raises(lbm.LBMError) as e:
+        L.adjoint(torch.zeros(3, N), 5)
+    assert e.value.status == -7
+    bad = rho0.copy()
+    bad[17] = np.nan
+    L.init(torch.as_tensor(bad), torch.as_tensor(u0))
+    with pytest.raises(lbm.LBMError) as e:
+        L.totals()
+    assert e.value.status == -6
+    C = lbm.LBM(q, *dims, 0.7, np.eye(3) / 3, check_every=2)
+    C.init(torch.as_tensor(bad), torch.as_tensor(u0))
+    with pytest.raises(lbm.LBMError) as e:
+        C.step(4)
+    assert e.value.status == -6
