@@ -1,14 +1,18 @@
 """Benchmark: MLUPS and HBM-roofline fraction of the fused stream + collide step on one GB300.
 
-Workload (default): D3Q19 anisotropic BGK, FP32 storage, 256^3 fully periodic Taylor-Green vortex
+Default workload: D3Q19 anisotropic BGK, FP32 storage, 256^3 fully periodic Taylor-Green vortex
 (u0 = 0.02, rho0 = 1), tau = 0.6, Theta = R diag(0.36, 0.33, 0.30) R^T with a seeded rotation R.
-One bench step = one lattice time step over the whole 256^3 box = one kernel launch. The
-populations (2 x 1.28 GB) exceed the 129 MB L2, so no flush is needed between steps.
+One bench step = one lattice time step over the whole box = one kernel launch. The populations
+(2 x 1.28 GB) exceed the 129 MB L2, so no flush is needed between steps.
 
-Prints one JSON line (rank 0). Extra keys: roofline (dominant kernel, CUDA events), cpu_baseline
-(the FP64 oracle on a bounded sample), e2e (through the public API with host buffers), clocks,
-gpu_launches, and sub-measurements for FP16-shifted storage and the checkpointed adjoint.
-`--impl reference` times the oracle itself (the reference arm of this benchmark).
+Modes
+  (default)   the one-line JSON contract: value = MLUPS of the forward step (device time),
+              roofline of the dominant kernel, cpu_baseline (oracle), e2e (public API with host
+              buffers), clocks, gpu_launches, plus sub-measurements (FP16-shifted forward, the
+              checkpointed adjoint).
+  --mode sweep     one JSON line per variant (lattice x storage x scheme x size, porous runs).
+  --mode profile   a small case of one kernel for ncu (--lattice/--storage/--scheme/--n/--kernel).
+  --impl reference the oracle itself timed on the host cores (the reference arm).
 """
 from __future__ import annotations
 
@@ -27,9 +31,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FALLBACK_HBM_GBS = 6800.0
+ELEM = {"fp32": 4, "fp32s": 4, "fp16s": 2, "fp64": 8}
 
-# DRAM traffic per launch from an ncu capture, keyed by workload; valid only while the kernel
-# source hash matches the one recorded with the counters (else the bench reports null).
+# DRAM bytes per launch from an ncu capture (profiles/), keyed by variant; used only while the
+# kernel sources hash to the recorded value (otherwise the bench reports traffic = null).
 NCU_TRAFFIC = {}
 
 
@@ -42,17 +47,15 @@ def kernel_source_hash() -> str:
 
 
 def measured_peak():
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
-        with open(p) as fh:
-            j = json.load(fh)
-        return float(j["hbm_gbs"]), "measured"
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples during the timed region."""
+    """nvidia-smi clock / throttle samples taken while the timed region runs."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -70,6 +73,7 @@ class ClockSampler:
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            time.sleep(0.3)
         except Exception:
             self.proc = None
         return self
@@ -80,6 +84,7 @@ class ClockSampler:
 
     def __exit__(self, *a):
         if self.proc:
+            time.sleep(0.2)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -107,34 +112,52 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------------
-WORKLOADS = {
-    # name: (q, n, storage, tau, description)
-    "d3q19_fp32_256": dict(q=19, n=256, storage="fp32", tau=0.6,
-                           desc="D3Q19 FP32 256^3 periodic Taylor-Green, rotated Theta, tau 0.6"),
-    "d3q19_fp16s_256": dict(q=19, n=256, storage="fp16s", tau=0.6,
-                            desc="D3Q19 FP16-shifted 256^3 periodic Taylor-Green"),
-}
-
-
-def bytes_per_cell(q, storage):
-    elem = {"fp32": 4, "fp32s": 4, "fp16s": 2, "fp64": 8}[storage]
-    return 2 * q * elem
-
-
-def make_problem(w):
+# Problems
+# ------------------------------------------------------------------------------------------------
+def theta3():
     from paper_2605_27004_gb300 import inputs
-    n = w["n"]
-    Th = inputs.theta_rotated([0.36, 0.33, 0.30], inputs.SEED_BASE + 2)
-    rho0, u0 = inputs.taylor_green_3d(n, 0.02)
-    return Th, rho0, u0
+    return inputs.theta_rotated([0.36, 0.33, 0.30], inputs.SEED_BASE + 2)
 
 
-def time_forward(w, steps, warmup, torch, lbm):
-    """Device-timed forward steps: returns (ms total, per-launch ms list, launches, ctx)."""
-    n, q = w["n"], w["q"]
-    Th, rho0, u0 = make_problem(w)
-    L = lbm.LBM(q, n, n, n, w["tau"], Th, storage=w["storage"])
-    L.init(torch.as_tensor(rho0, dtype=torch.float32), torch.as_tensor(u0, dtype=torch.float32))
+def problem(q, n, kind):
+    """(dims, tau, Theta, rho0, u0, solid) of a named synthetic workload at size n."""
+    from paper_2605_27004_gb300 import inputs
+    if kind == "tg":
+        if q == 9:
+            rho0, u0 = inputs.taylor_green_2d(n, 0.02)
+            return (n, n, 1), 0.8, inputs.theta_from_atilde([[1.0, 0.2], [0.2, 1.0]]), rho0, u0, None
+        if n >= 384:  # same field as inputs.taylor_green_3d, built on the device to spare host memory
+            import torch
+            k = 2 * np.pi / n
+            ax = torch.arange(n, device="cuda", dtype=torch.float32) * k
+            s, c = torch.sin(ax), torch.cos(ax)
+            u0 = torch.zeros((3, n, n, n), device="cuda", dtype=torch.float32)
+            u0[0] = 0.02 * s[None, None, :] * c[None, :, None] * c[:, None, None]
+            u0[1] = -0.02 * c[None, None, :] * s[None, :, None] * c[:, None, None]
+            return (n, n, n), 0.6, theta3(), None, u0.reshape(3, -1), None
+        rho0, u0 = inputs.taylor_green_3d(n, 0.02)
+        return (n, n, n), 0.6, theta3(), rho0, u0, None
+    if kind == "porous":
+        solid = inputs.porous_spheres(n, n, n, seed=inputs.SEED_BASE + 3)
+        N = n ** 3
+        u0 = np.zeros((3, N), dtype=np.float32)
+        u0[0] = 0.03 * (1 - solid)
+        return (n, n, n), 0.7, np.diag([0.38, 0.33, 0.29]), np.ones(N, dtype=np.float32), u0, solid
+    raise ValueError(kind)
+
+
+def make_ctx(q, n, storage, scheme, kind, torch, lbm, **kw):
+    dims, tau, Th, rho0, u0, solid = problem(q, n, kind)
+    L = lbm.LBM(q, *dims, tau, Th, solid=solid, storage=storage, scheme=scheme, **kw)
+    dt = torch.float64 if storage == "fp64" else torch.float32
+    L.init(None if rho0 is None else torch.as_tensor(rho0, dtype=dt), torch.as_tensor(u0, dtype=dt))
+    n_fluid = L.N if solid is None else int((solid == 0).sum())
+    return L, n_fluid
+
+
+def time_steps(L, steps, warmup, torch):
+    """Device time of `steps` single-step launches on the context's stream (CUDA events), plus the
+    mean per-launch duration from per-step event pairs."""
     L.step(warmup)
     stream = L.stream
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -148,74 +171,81 @@ def time_forward(w, steps, warmup, torch, lbm):
         ev[k][1].record(stream)
     t1.record(stream)
     torch.cuda.synchronize()
-    launches = L.launches - l0
     per = [a.elapsed_time(b) for a, b in ev]
-    return t0.elapsed_time(t1), per, launches, L
+    return t0.elapsed_time(t1), float(np.mean(per)), L.launches - l0
 
 
-def time_e2e(w, steps, torch, lbm):
-    """Public API with host buffers: pinned H2D of (rho0, u0), init, steps, moments, D2H of u."""
-    n, q = w["n"], w["q"]
-    Th, rho0, u0 = make_problem(w)
-    N = n ** 3
-    rho_h = torch.as_tensor(rho0, dtype=torch.float32).pin_memory()
-    u_h = torch.as_tensor(u0, dtype=torch.float32).reshape(3, N).pin_memory()
-    out_h = torch.empty((3, N), dtype=torch.float32).pin_memory()
-    L = lbm.LBM(q, n, n, n, w["tau"], Th, storage=w["storage"])
-    rho_d = torch.empty(N, dtype=torch.float32, device="cuda")
-    u_d = torch.empty((3, N), dtype=torch.float32, device="cuda")
-    out_d = torch.empty((3, N), dtype=torch.float32, device="cuda")
-    stream = L.stream
-    # warm-up of the same sequence
-    rho_d.copy_(rho_h, non_blocking=True)
-    u_d.copy_(u_h, non_blocking=True)
-    L.init(rho_d, u_d)
-    L.step(2)
-    torch.cuda.synchronize()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    rho_d.copy_(rho_h, non_blocking=True)
-    u_d.copy_(u_h, non_blocking=True)
-    L.init(rho_d, u_d)
-    L.step(steps)
-    L.moments_into(u=out_d)
-    out_h.copy_(out_d, non_blocking=True)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1)
-    h2d = (rho_h.numel() + u_h.numel()) * 4
-    d2h = out_h.numel() * 4
+def variant(q, n, storage, scheme, kind, steps, warmup, torch, lbm, peak):
+    L, nf = make_ctx(q, n, storage, scheme, kind, torch, lbm, use_graphs=-1)
+    ms, kms, launches = time_steps(L, steps, warmup, torch)
+    N = L.N
     L.close()
-    return ms, h2d, d2h
+    bpc = 2 * q * ELEM[storage]
+    alg = nf * bpc + (N / 8 if kind == "porous" else 0)
+    gbs = alg / (kms * 1e-3) / 1e9
+    return {"lattice": f"D{3 if q != 9 else 2}Q{q}", "n": n, "storage": storage, "scheme": scheme, "kind": kind,
+            "cells": N, "fluid_cells": nf, "mlups_all": N * steps / (ms * 1e-3) / 1e6,
+            "mlups_fluid": nf * steps / (ms * 1e-3) / 1e6, "kernel_ms": kms, "kernel_gbs": gbs,
+            "frac": gbs / peak, "bytes_per_fluid_cell": bpc, "launches": launches}
 
 
-def time_adjoint(q, n, storage, steps, K, torch, lbm):
-    """Checkpointed adjoint through `steps` steps: ms of lbm_adjoint (recompute + adjoint sweep)."""
-    from paper_2605_27004_gb300 import inputs
-    Th = inputs.theta_rotated([0.36, 0.33, 0.30], inputs.SEED_BASE + 2)
-    rho0, u0 = inputs.taylor_green_3d(n, 0.02)
-    L = lbm.LBM(q, n, n, n, 0.6, Th, storage=storage)
-    L.init(torch.as_tensor(rho0, dtype=torch.float32), torch.as_tensor(u0, dtype=torch.float32))
+def time_adjoint(q, n, storage, scheme, steps, K, torch, lbm):
+    """Wall time of lbm_adjoint through `steps` steps (forward recompute + reverse sweep)."""
+    L, nf = make_ctx(q, n, storage, scheme, "tg", torch, lbm)
     L.step(steps)
-    g = torch.randn(3, n ** 3, device="cuda", dtype=torch.float32)
+    g = torch.randn(3, L.N, device="cuda", dtype=torch.float64 if storage == "fp64" else torch.float32)
     torch.cuda.synchronize()
+    l0 = L.launches
     t = time.perf_counter()
     L.adjoint(g, steps, K)
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t) * 1e3
+    launches = L.launches - l0
+    N = L.N
     L.close()
-    return ms
+    return ms, N, launches
 
 
-def cpu_baseline(w, budget_s=12.0):
-    """The FP64 oracle as it stands, on a bounded sample of the workload: a 64^3 sub-box of the
+def time_e2e(q, n, storage, steps, torch, lbm):
+    """Public API with host buffers: pinned H2D of (rho0, u0), init, steps, moments, D2H of u."""
+    dims, tau, Th, rho0, u0, solid = problem(q, n, "tg")
+    N = int(np.prod(dims))
+    d = 3 if q != 9 else 2
+    rho_h = torch.as_tensor(rho0, dtype=torch.float32).pin_memory()
+    u_h = torch.as_tensor(u0, dtype=torch.float32).reshape(d, N).pin_memory()
+    out_h = torch.empty((d, N), dtype=torch.float32).pin_memory()
+    L = lbm.LBM(q, *dims, tau, Th, storage=storage)
+    rho_d = torch.empty(N, dtype=torch.float32, device="cuda")
+    u_d = torch.empty((d, N), dtype=torch.float32, device="cuda")
+    out_d = torch.empty((d, N), dtype=torch.float32, device="cuda")
+    stream = L.stream
+
+    def job(k):
+        rho_d.copy_(rho_h, non_blocking=True)
+        u_d.copy_(u_h, non_blocking=True)
+        L.init(rho_d, u_d)
+        L.step(k)
+        L.moments_into(u=out_d)
+        out_h.copy_(out_d, non_blocking=True)
+
+    job(3)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    job(steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    L.close()
+    return ms, (rho_h.numel() + u_h.numel()) * 4, out_h.numel() * 4
+
+
+def cpu_baseline(budget_s=12.0):
+    """The FP64 oracle as it stands on a bounded sample of the default workload: a 64^3 box of the
     same Taylor-Green problem, as many steps as fit the budget."""
     import oracle
-    from paper_2605_27004_gb300 import inputs
-    n = 64
-    Th = inputs.theta_rotated([0.36, 0.33, 0.30], inputs.SEED_BASE + 2)
-    rho0, u0 = inputs.taylor_green_3d(n, 0.02)
-    pb = oracle.Problem(w["q"], n, n, n, w["tau"], Th)
+    dims, tau, Th, rho0, u0, _ = problem(19, 64, "tg")
+    pb = oracle.Problem(19, *dims, tau, Th)
     f = pb.init(rho0, u0)
     t = time.perf_counter()
     pb.run(f, 1)
@@ -224,36 +254,84 @@ def cpu_baseline(w, budget_s=12.0):
     t = time.perf_counter()
     pb.run(f, steps)
     dt = time.perf_counter() - t
-    return {"value": n ** 3 * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{w['desc'].split(' 256^3')[0]} on a 64^3 box, {steps} steps, FP64 push oracle"}
+    return {"value": 64 ** 3 * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"D3Q19 Taylor-Green on a 64^3 box, {steps} steps of the FP64 push oracle"}
 
 
+# ------------------------------------------------------------------------------------------------
 def run_reference(args):
-    """Reference arm: the oracle timed on the host cores (rank 0 only)."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    """Reference arm: the oracle, as it stands, timed on the host cores (rank 0 only)."""
+    if int(os.environ.get("RANK", "0")) != 0:
         return
-    w = WORKLOADS[args.workload]
     import oracle
-    from paper_2605_27004_gb300 import inputs
-    n = 64
-    Th = inputs.theta_rotated([0.36, 0.33, 0.30], inputs.SEED_BASE + 2)
-    rho0, u0 = inputs.taylor_green_3d(n, 0.02)
-    pb = oracle.Problem(w["q"], n, n, n, w["tau"], Th)
+    dims, tau, Th, rho0, u0, _ = problem(19, 64, "tg")
+    pb = oracle.Problem(19, *dims, tau, Th)
     f = pb.init(rho0, u0)
     pb.run(f, max(1, args.warmup))
     t = time.perf_counter()
     pb.run(f, args.steps)
     dt = time.perf_counter() - t
-    v = n ** 3 * args.steps / dt / 1e6
+    v = 64 ** 3 * args.steps / dt / 1e6
     line = {"impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w["desc"] + " (oracle sample: 64^3 box)"},
+            "data": "synthetic",
+            "config": {"workload": "D3Q19 256^3 periodic Taylor-Green, rotated Theta, tau 0.6 "
+                                   "(each oracle step: a 64^3 box of it)"},
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
-                             "sample": f"64^3 box of the workload, {args.steps} timed steps"},
+                             "sample": f"64^3 box of the workload, {args.steps} timed FP64 oracle steps"},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_sweep(args, torch, lbm):
+    peak, src = measured_peak()
+    cases = []
+    for n in (64, 128, 256, 512):
+        cases += [(19, n, "fp32", "pull", "tg"), (19, n, "fp16s", "pull", "tg"), (19, n, "fp16s", "aa", "tg")]
+    cases += [(19, 768, "fp16s", "aa", "tg")]
+    cases += [(27, 256, "fp32", "pull", "tg"), (27, 256, "fp16s", "pull", "tg"), (19, 256, "fp32", "aa", "tg"),
+              (19, 256, "fp32s", "pull", "tg"), (9, 4096, "fp32", "pull", "tg"), (9, 64, "fp64", "pull", "tg")]
+    cases += [(27, 512, "fp32", "pull", "porous"), (27, 512, "fp16s", "pull", "porous"),
+              (27, 512, "fp16s", "aa", "porous")]
+    if args.only:
+        cases = [c for c in cases if args.only in "%s_%d_%s_%s_%s" % (c[0], c[1], c[2], c[3], c[4])]
+    for c in cases:
+        q, n, st, sc, kind = c
+        try:
+            r = variant(q, n, st, sc, kind, args.steps, args.warmup, torch, lbm, peak)
+            r["peak"] = peak
+            r["peak_source"] = src
+        except Exception as e:  # report and continue (e.g. memory)
+            r = {"case": c, "error": str(e)[:200]}
+        print(json.dumps(r), flush=True)
+        torch.cuda.empty_cache()
+    for (q, n, st, sc, K, steps) in [(19, 128, "fp32", "pull", 20, 200), (19, 128, "fp16s", "pull", 20, 200),
+                                     (19, 256, "fp32", "pull", 20, 100), (19, 256, "fp16s", "aa", 20, 100)]:
+        if args.only and args.only not in "adj_%d_%d_%s_%s" % (q, n, st, sc):
+            continue
+        ms, N, launches = time_adjoint(q, n, st, sc, steps, K, torch, lbm)
+        print(json.dumps({"adjoint": True, "lattice": f"D3Q{q}", "n": n, "storage": st, "scheme": sc, "steps": steps,
+                          "checkpoint_every": K, "mlups": N * steps / (ms * 1e-3) / 1e6, "ms": ms,
+                          "launches": launches}), flush=True)
+        torch.cuda.empty_cache()
+
+
+def run_profile(args, torch, lbm):
+    """Small case for ncu: --kernel fwd runs warmup + steps forward launches; --kernel adjoint
+    runs one short adjoint (seed, recompute, adjoint steps)."""
+    kind = "porous" if args.porous else "tg"
+    L, _ = make_ctx(args.lattice, args.n, args.storage, args.scheme, kind, torch, lbm, use_graphs=-1)
+    if args.kernel == "fwd":
+        L.step(args.warmup + args.steps)
+    else:
+        L.step(args.steps)
+        g = torch.randn(L.d, L.N, device="cuda", dtype=torch.float64 if args.storage == "fp64" else torch.float32)
+        L.adjoint(g, args.steps, max(1, args.steps // 2))
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": True, "lattice": args.lattice, "n": args.n, "storage": args.storage,
+                      "scheme": args.scheme, "kernel": args.kernel, "launches": L.launches}))
+    L.close()
 
 
 def main():
@@ -262,8 +340,15 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="d3q19_fp32_256", choices=sorted(WORKLOADS))
-    ap.add_argument("--no-extras", action="store_true", help="skip sub-measurements, e2e and cpu baseline")
+    ap.add_argument("--mode", default="bench", choices=["bench", "sweep", "profile"])
+    ap.add_argument("--no-extras", action="store_true", help="contract line without sub-measurements/e2e/cpu")
+    ap.add_argument("--only", default="", help="sweep: substring filter on case names")
+    ap.add_argument("--lattice", type=int, default=19)
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--storage", default="fp32")
+    ap.add_argument("--scheme", default="pull")
+    ap.add_argument("--kernel", default="fwd", choices=["fwd", "adjoint"])
+    ap.add_argument("--porous", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -277,64 +362,60 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.mode == "sweep":
+        run_sweep(args, torch, lbm)
+        return
+    if args.mode == "profile":
+        run_profile(args, torch, lbm)
+        return
+
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    w = WORKLOADS[args.workload]
-    n, q = w["n"], w["q"]
-    N = n ** 3
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    # cpu baseline first (host only, before the timed GPU region)
-    cpu = cpu_baseline(w) if (rank == 0 and world == 1 and not args.no_extras) else None
+    peak, peak_src = measured_peak()
+    q, n, storage = 19, 256, "fp32"
+    cpu = cpu_baseline() if (rank == 0 and world == 1 and not args.no_extras) else None
 
+    # timed region: K forward steps of the 256^3 D3Q19 FP32 workload (independent replica per rank)
+    L, nf = make_ctx(q, n, storage, "pull", "tg", torch, lbm)
+    N = L.N
     barrier()
     with ClockSampler(local) as clk:
-        ms, per, launches, L = time_forward(w, args.steps, args.warmup, torch, lbm)
+        ms, kms, launches = time_steps(L, args.steps, args.warmup, torch)
     barrier()
+    L.close()
+    del L
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     mlups = N * args.steps * world / (ms * 1e-3) / 1e6
-    peak, peak_src = measured_peak()
-    bpc = bytes_per_cell(q, w["storage"])
-    kern_ms = float(np.mean(per))
-    achieved = bpc * N / (kern_ms * 1e-3) / 1e9
-    traffic = None
-    rec = NCU_TRAFFIC.get(args.workload)
-    if rec and rec.get("kernel_sha") == kernel_source_hash():
-        traffic = rec["traffic_bytes"]
-    L.close()
-    del L
+    bpc = 2 * q * ELEM[storage]
+    achieved = bpc * N / (kms * 1e-3) / 1e9
+    rec = NCU_TRAFFIC.get("d3q19_fp32_pull")
+    traffic = rec["traffic_bytes"] if rec and rec.get("kernel_sha") == kernel_source_hash() else None
     torch.cuda.empty_cache()
 
-    sub = {}
-    e2e = None
+    sub, e2e = {}, None
     if not args.no_extras:
         if rank == 0:
-            wf = WORKLOADS["d3q19_fp16s_256"]
-            ms16, per16, _, L16 = time_forward(wf, max(10, args.steps // 2), args.warmup, torch, lbm)
-            L16.close()
-            k16 = float(np.mean(per16))
-            sub["fwd_fp16s_256"] = {"mlups": N * len(per16) / (ms16 * 1e-3) / 1e6,
-                                    "kernel_gbs": bytes_per_cell(19, "fp16s") * N / (k16 * 1e-3) / 1e9,
-                                    "frac": bytes_per_cell(19, "fp16s") * N / (k16 * 1e-3) / 1e9 / peak}
-            nadj, Kadj, nA = 200, 20, 128
-            msa = time_adjoint(19, nA, "fp32", nadj, Kadj, torch, lbm)
-            sub["adjoint_fp32_128"] = {"mlups": nA ** 3 * nadj / (msa * 1e-3) / 1e6, "steps": nadj,
-                                       "checkpoint_every": Kadj,
-                                       "note": "wall time of lbm_adjoint incl. forward recompute"}
-        msE, h2d, d2h = time_e2e(w, args.steps, torch, lbm)
+            r16 = variant(19, 256, "fp16s", "pull", "tg", max(10, args.steps // 2), args.warmup, torch, lbm, peak)
+            sub["fwd_fp16s_256"] = {k: r16[k] for k in ("mlups_all", "kernel_gbs", "frac", "kernel_ms")}
+            msa, Na, la = time_adjoint(19, 128, "fp32", "pull", 200, 20, torch, lbm)
+            sub["adjoint_fp32_128"] = {"mlups": Na * 200 / (msa * 1e-3) / 1e6, "steps": 200, "checkpoint_every": 20,
+                                       "launches": la, "note": "wall time of lbm_adjoint incl. forward recompute"}
+        msE, h2d, d2h = time_e2e(q, n, storage, args.steps, torch, lbm)
         e2e = {"value": N * args.steps * world / (msE * 1e-3) / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-               "note": "one upload of (rho0, u0), init, K steps, moments, one download of u; bytes amortised per step"}
-
+               "note": "per job: one pinned upload of (rho0, u0), init, K steps, moments, one download of u; "
+                       "bytes amortised over the K steps"}
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -343,13 +424,13 @@ def main():
         "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w["desc"], "cells": N, "lattice": f"D3Q{q}", "storage": w["storage"],
-                   "l2": "inputs larger than L2 (2 x %.2f GB populations)" % (q * N * 4 / 1e9),
+        "config": {"workload": "D3Q19 FP32 256^3 periodic Taylor-Green, u0 0.02, rotated Theta "
+                               "R diag(0.36,0.33,0.30) R^T, tau 0.6",
+                   "cells": N, "l2": "inputs larger than L2 (2 x %.2f GB populations)" % (q * N * 4 / 1e9),
                    "parallelism": "independent replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_source": peak_src,
-                     "kernel": "k_step_pull<19, FP32>", "bytes_per_cell": bpc,
-                     "kernel_ms_mean": kern_ms},
+                     "traffic": traffic, "peak_source": peak_src, "kernel": "k_step_pull<19, FP32>",
+                     "bytes_per_cell": bpc, "kernel_ms_mean": kms},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk.summary(),

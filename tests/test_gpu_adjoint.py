@@ -70,8 +70,12 @@ def test_adjoint_reduced_precision(storage):
     """FP32 adjoint (FP64 gradient accumulation) against the FP64 oracle adjoint on 24^3, 60 steps."""
     q, dims = 19, (24, 24, 24)
     dth, dtau, du0, odth, odtau, odu0 = _run(q, dims, None, storage, "pull", 10, 60)
-    tol = 1e-3 if storage != "fp16s" else 2e-2
     print(storage, np.abs(dth - odth).max() / np.abs(odth).max(), abs(dtau - odtau) / abs(odtau), rel_l2(du0, odu0))
-    assert np.abs(dth - odth).max() <= tol * np.abs(odth).max()
-    assert abs(dtau - odtau) <= tol * abs(odtau)
-    assert rel_l2(du0, odu0) < tol
+    assert np.abs(dth - odth).max() <= 1e-3 * np.abs(odth).max()
+    assert rel_l2(du0, odu0) < 1e-3
+    # dL/dtau weighs the non-equilibrium part f - feq, which is O(Kn) small; FP16 storage rounds
+    # f - r to 11 bits, i.e. a relative error of ~1e-3 of the O(u) deviation, which is a few
+    # percent of f - feq. The adjoint differentiates the stored trajectory, so the gap is the
+    # forward precision, not the adjoint.
+    tol_tau = 1e-3 if storage != "fp16s" else 5e-2
+    assert abs(dtau - odtau) <= tol_tau * abs(odtau)
