@@ -192,6 +192,7 @@ def variant(q, n, storage, scheme, kind, steps, warmup, torch, lbm, peak):
 def time_adjoint(q, n, storage, scheme, steps, K, torch, lbm):
     """Wall time of lbm_adjoint through `steps` steps (forward recompute + reverse sweep)."""
     L, nf = make_ctx(q, n, storage, scheme, "tg", torch, lbm)
+    L.record_checkpoints(K)  # the forward run keeps the checkpoints the adjoint starts from
     L.step(steps)
     g = torch.randn(3, L.N, device="cuda", dtype=torch.float64 if storage == "fp64" else torch.float32)
     torch.cuda.synchronize()

@@ -121,11 +121,20 @@ int lbm_populations(lbm_ctx* ctx, void* f);
  * has rho <= 0 or a non-finite moment. */
 int lbm_totals(lbm_ctx* ctx, double* mass, double* momentum);
 
+/* Keep the stored state at every multiple of checkpoint_every steps of the current trajectory
+ * (from lbm_init on; 0 stops recording), in device memory while adjoint_mem_limit allows and in
+ * pinned host memory beyond. A following lbm_adjoint with the same checkpoint_every then
+ * recomputes only inside segments instead of re-running the whole forward pass. Call it before
+ * lbm_init or right after it (step 0). */
+int lbm_record_checkpoints(lbm_ctx* ctx, int checkpoint_every);
+
 /* Discrete adjoint of f(0) = feq(rho0, u0) -> f(n) -> u(n) for a loss L(u(n)) with
  * loss_grad = dL/du(n) (device [d][N], field type). Requires exactly n steps since the last
- * lbm_init (else LBM_ERR_NO_FORWARD). The trajectory is recomputed from the initial fields with
- * checkpoints every checkpoint_every steps (0: about sqrt(n)); it leaves f(n) in place.
- * Results are read with lbm_gradients. */
+ * lbm_init (else LBM_ERR_NO_FORWARD). Works backward in segments of checkpoint_every steps
+ * (0: the recorded interval, else about sqrt(n)): each segment is recomputed from its checkpoint
+ * (recorded by lbm_record_checkpoints, or taken here by a forward pass from the initial fields)
+ * and then swept by one adjoint kernel per step. Leaves f(n) in place. Results are read with
+ * lbm_gradients. Synchronises. */
 int lbm_adjoint(lbm_ctx* ctx, const void* loss_grad, int n, int checkpoint_every);
 
 /* Gradients of the last lbm_adjoint: dTheta (host, 3 values in 2D: xx, yy, xy; 6 in 3D:

@@ -97,7 +97,7 @@ struct lbm_ctx {
 
     Geom geom{};
     Shape shape{};
-    uint32_t* mask = nullptr;
+    uint32_t* link = nullptr;  // per-cell link words (N), null for an all-fluid box
     long long n_fluid = 0;
 
     Coef<double> cd{};
@@ -129,6 +129,12 @@ struct lbm_ctx {
     // graphs
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
+
+    // checkpoints recorded during the forward run (state at t = k * rec_K)
+    int rec_K = 0;
+    std::vector<void*> rec_ptr;
+    std::vector<bool> rec_host;
+    long long rec_valid = 0;  // checkpoints 0 .. rec_valid-1 hold the current trajectory
 
     size_t dev_bytes = 0;
     long long launches = 0;
@@ -328,6 +334,52 @@ int ensure_graph(lbm_ctx* c, int gsteps) {
     return LBM_OK;
 }
 
+// Checkpoint k of the recorded trajectory: device memory while the adjoint limit allows, else
+// pinned host memory. Returns null on allocation failure.
+void* ckpt_slot(lbm_ctx* c, size_t k, bool* host) {
+    const size_t SB = c->state_bytes();
+    if (k < c->rec_ptr.size() && c->rec_ptr[k]) {
+        *host = c->rec_host[k];
+        return c->rec_ptr[k];
+    }
+    if (c->rec_ptr.size() <= k) {
+        c->rec_ptr.resize(k + 1, nullptr);
+        c->rec_host.resize(k + 1, false);
+    }
+    size_t limit = c->opt.adjoint_mem_limit;
+    size_t fr = 0, tot = 0;
+    if (limit == 0 && cudaMemGetInfo(&fr, &tot) == cudaSuccess) limit = fr > ((size_t)4 << 30) ? fr - ((size_t)4 << 30) : 0;
+    size_t used = 0;
+    for (size_t j = 0; j < c->rec_ptr.size(); ++j)
+        if (c->rec_ptr[j] && !c->rec_host[j]) used += SB;
+    void* p = nullptr;
+    bool h = false;
+    if (used + SB <= limit) p = dev_alloc(c, SB);
+    if (!p) {
+        if (cudaMallocHost(&p, SB) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        h = true;
+    }
+    c->rec_ptr[k] = p;
+    c->rec_host[k] = h;
+    *host = h;
+    return p;
+}
+
+int record_ckpt(lbm_ctx* c) {
+    if (c->rec_K <= 0 || c->steps % c->rec_K != 0) return LBM_OK;
+    const long long k = c->steps / c->rec_K;
+    if (k != c->rec_valid) return LBM_OK;  // only extend a contiguous record
+    bool host = false;
+    void* p = ckpt_slot(c, (size_t)k, &host);
+    if (!p) return fail(c, LBM_ERR_OOM, "checkpoint %lld", k);
+    LBM_CUDA(c, cudaMemcpyAsync(p, state_ptr(c), c->state_bytes(), cudaMemcpyDefault, c->stream));
+    c->rec_valid = k + 1;
+    return LBM_OK;
+}
+
 int check_flag(lbm_ctx* c) {
     LBM_CUDA(c, cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -389,7 +441,14 @@ void lbm_destroy(lbm_ctx* c) {
     const size_t SB = c->state_bytes();
     dev_free(c, c->pop[0], SB);
     dev_free(c, c->pop[1], SB);
-    dev_free(c, c->mask, (size_t)c->geom.W * c->ny * c->nz * 4);
+    dev_free(c, c->link, (size_t)c->N * 4);
+    for (size_t k = 0; k < c->rec_ptr.size(); ++k) {
+        if (!c->rec_ptr[k]) continue;
+        if (c->rec_host[k])
+            cudaFreeHost(c->rec_ptr[k]);
+        else
+            dev_free(c, c->rec_ptr[k], c->state_bytes());
+    }
     dev_free(c, c->rho_init, (size_t)c->N * c->felem);
     dev_free(c, c->u_init, (size_t)c->N * c->d * c->felem);
     dev_free(c, c->flag, sizeof(int) * 2);
@@ -458,39 +517,40 @@ int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau
     c->stream = (cudaStream_t)c->opt.stream;
     build_coef(c);
 
+    if (c->N >= (1LL << 31)) return bail(fail(c, LBM_ERR_INVALID_ARG, "more than 2^31 - 1 cells"));
     c->geom.nx = nx;
     c->geom.ny = ny;
     c->geom.nz = nz;
-    c->geom.N = c->N;
-    c->geom.W = (nx + 31) / 32;
-    c->geom.mask = nullptr;
+    c->geom.N = (uint32_t)c->N;
+    c->geom.link = nullptr;
     c->shape = shape_for(c->geom);
     c->n_fluid = c->N;
 
     if (solid_mask) {
         std::vector<uint8_t> m((size_t)c->N);
-        if (is_device_ptr(solid_mask)) {
+        const bool on_dev = is_device_ptr(solid_mask);
+        if (on_dev) {
             if (cudaMemcpy(m.data(), solid_mask, (size_t)c->N, cudaMemcpyDeviceToHost) != cudaSuccess)
                 return bail(cuda_fail(c, cudaGetLastError(), "copy of the solid mask"));
         } else {
             std::memcpy(m.data(), solid_mask, (size_t)c->N);
         }
-        const size_t rows = (size_t)ny * nz, W = (size_t)c->geom.W;
-        std::vector<uint32_t> bits(rows * W, 0u);
         long long nsolid = 0;
-        for (size_t r = 0; r < rows; ++r)
-            for (int x = 0; x < nx; ++x)
-                if (m[r * nx + x]) {
-                    bits[r * W + x / 32] |= 1u << (x % 32);
-                    ++nsolid;
-                }
+        for (size_t n = 0; n < (size_t)c->N; ++n) nsolid += m[n] != 0;
         c->n_fluid = c->N - nsolid;
         if (nsolid > 0) {
-            c->mask = (uint32_t*)dev_alloc(c, rows * W * 4);
-            if (!c->mask) return bail(fail(c, LBM_ERR_OOM, "mask allocation"));
-            if (cudaMemcpy(c->mask, bits.data(), rows * W * 4, cudaMemcpyHostToDevice) != cudaSuccess)
-                return bail(cuda_fail(c, cudaGetLastError(), "mask upload"));
-            c->geom.mask = c->mask;
+            c->link = (uint32_t*)dev_alloc(c, (size_t)c->N * 4);
+            uint8_t* dmask = (uint8_t*)dev_alloc(c, (size_t)c->N);
+            if (!c->link || !dmask) {
+                dev_free(c, dmask, (size_t)c->N);
+                return bail(fail(c, LBM_ERR_OOM, "link-mask allocation"));
+            }
+            cudaError_t e = cudaMemcpyAsync(dmask, m.data(), (size_t)c->N, cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess) e = c->ops->link_mask(c->geom, dmask, c->link, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            dev_free(c, dmask, (size_t)c->N);
+            if (e != cudaSuccess) return bail(cuda_fail(c, e, "link-mask construction"));
+            c->geom.link = c->link;
         }
     }
     const size_t SB = c->state_bytes();
@@ -531,6 +591,7 @@ int lbm_set_params(lbm_ctx* c, double tau, const double* Theta) {
     c->state_valid = false;
     c->init_fields = false;
     c->grads_ready = false;
+    c->rec_valid = 0;
     return LBM_OK;
 }
 
@@ -555,6 +616,15 @@ int lbm_init(lbm_ctx* c, const void* rho, const void* u) {
     c->state_valid = true;
     c->init_fields = true;
     c->grads_ready = false;
+    c->rec_valid = 0;
+    return record_ckpt(c);
+}
+
+int lbm_record_checkpoints(lbm_ctx* c, int checkpoint_every) {
+    if (!c || checkpoint_every < 0) return LBM_ERR_INVALID_ARG;
+    c->rec_K = checkpoint_every;
+    c->rec_valid = 0;
+    if (checkpoint_every > 0 && c->state_valid && c->steps == 0 && c->init_fields) return record_ckpt(c);
     return LBM_OK;
 }
 
@@ -564,12 +634,14 @@ int lbm_step(lbm_ctx* c, int n) {
     const int gsteps = 16;
     bool graphs = c->opt.use_graphs > 0 || (c->opt.use_graphs == 0 && c->N <= (1LL << 21));
     long long next_check = c->opt.check_every > 0 ? (c->steps / c->opt.check_every + 1) * c->opt.check_every : -1;
+    const bool recording = c->rec_K > 0 && c->rec_valid * c->rec_K > c->steps;
+    long long next_rec = recording ? (c->steps / c->rec_K + 1) * c->rec_K : -1;
     int left = n;
     while (left > 0) {
         const bool aligned = (c->steps & 1) == 0 && (c->scheme != LBM_PULL2 || c->cur == 0);
         bool ran = false;
-        if (graphs && left >= gsteps && aligned &&
-            (next_check < 0 || c->steps + gsteps <= next_check)) {
+        if (graphs && left >= gsteps && aligned && (next_check < 0 || c->steps + gsteps <= next_check) &&
+            (next_rec < 0 || c->steps + gsteps <= next_rec)) {
             int rc = ensure_graph(c, gsteps);
             if (rc) return rc;
             LBM_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
@@ -587,6 +659,11 @@ int lbm_step(lbm_ctx* c, int n) {
             int rc = check_flag(c);
             if (rc) return rc;
             next_check += c->opt.check_every;
+        }
+        if (next_rec >= 0 && c->steps >= next_rec) {
+            int rc = record_ckpt(c);
+            if (rc) return rc;
+            next_rec += c->rec_K;
         }
     }
     return LBM_OK;
@@ -642,7 +719,7 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
     if (!c->init_fields || !c->state_valid || c->steps != n)
         return fail(c, LBM_ERR_NO_FORWARD, "adjoint over %d steps but %lld steps were run since lbm_init", n,
                     (long long)c->steps);
-    if (K == 0) K = std::max(1, (int)std::lround(std::sqrt((double)std::max(n, 1))));
+    if (K == 0) K = c->rec_K > 0 ? c->rec_K : std::max(1, (int)std::lround(std::sqrt((double)std::max(n, 1))));
     K = std::max(1, std::min(K, std::max(n, 1)));
     const size_t SB = c->state_bytes();
     const size_t LB = (size_t)c->q * c->N * c->felem;
@@ -660,125 +737,131 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
     c->grads_ready = false;
 
     const int C = (n + K - 1) / K;  // checkpoints at t = 0, K, ..., (C-1)K
-    // Memory: C checkpoints + (K - 1) segment states + 2 stepping buffers.
-    size_t limit = c->opt.adjoint_mem_limit;
-    if (limit == 0) {
-        size_t fr = 0, tot = 0;
-        LBM_CUDA(c, cudaMemGetInfo(&fr, &tot));
-        const size_t margin = (size_t)2 << 30;
-        limit = fr > margin ? fr - margin : 0;
-    }
+    // Recorded checkpoints of the forward run are used when they cover [0, n) with this K.
+    const bool recorded = c->rec_K == K && c->rec_valid >= C;
     const int nseg = std::max(K - 1, 0);
-    const int nstep_buf = 2;
-    const bool ckpt_on_device = (size_t)(C + nseg + nstep_buf) * SB <= limit;
-    if ((size_t)(nseg + nstep_buf) * SB > limit)
-        return fail(c, LBM_ERR_OOM, "adjoint segment of %d states (%zu bytes each) exceeds the memory limit", K, SB);
-
     std::vector<void*> ckpt(C, nullptr), seg(nseg, nullptr);
-    void* stepbuf[2] = {nullptr, nullptr};
-    bool host_ckpt = !ckpt_on_device;
-    int rc = LBM_OK;
+    std::vector<bool> ckpt_host(C, false);
+    void* base = nullptr;    // device copy of a host checkpoint (segment start)
+    void* fwd[2] = {nullptr, nullptr};
+    std::vector<void*> own;  // checkpoints this call allocated
+    std::vector<bool> own_host;
     auto release = [&]() {
         cudaStreamSynchronize(c->stream);
-        for (void* p : ckpt)
-            if (p) {
-                if (host_ckpt)
-                    cudaFreeHost(p);
-                else
-                    dev_free(c, p, SB);
-            }
+        for (size_t k = 0; k < own.size(); ++k) {
+            if (own_host[k])
+                cudaFreeHost(own[k]);
+            else
+                dev_free(c, own[k], SB);
+        }
         for (void* p : seg) dev_free(c, p, SB);
-        dev_free(c, stepbuf[0], SB);
-        dev_free(c, stepbuf[1], SB);
+        dev_free(c, base, SB);
+        dev_free(c, fwd[0], SB);
+        dev_free(c, fwd[1], SB);
     };
-    for (int k = 0; k < C; ++k) {
-        if (host_ckpt) {
-            if (cudaMallocHost(&ckpt[k], SB) != cudaSuccess) {
-                ckpt[k] = nullptr;
-                release();
-                return fail(c, LBM_ERR_OOM, "host checkpoint %d of %zu bytes", k, SB);
-            }
-        } else if (!(ckpt[k] = dev_alloc(c, SB))) {
-            release();
-            return fail(c, LBM_ERR_OOM, "device checkpoint %d", k);
-        }
-    }
-    for (int k = 0; k < nseg; ++k)
-        if (!(seg[k] = dev_alloc(c, SB))) {
-            release();
-            return fail(c, LBM_ERR_OOM, "segment state %d", k);
-        }
-    stepbuf[0] = dev_alloc(c, SB);
-    stepbuf[1] = dev_alloc(c, SB);
-    if (!stepbuf[0] || !stepbuf[1]) {
-        release();
-        return fail(c, LBM_ERR_OOM, "adjoint stepping buffers");
-    }
-    for (int k = 0; k < 2; ++k)
-        if (cudaMemsetAsync(stepbuf[k], 0, SB, c->stream) != cudaSuccess) {
-            release();
-            return cuda_fail(c, cudaGetLastError(), "clear stepping buffer");
-        }
-    for (int k = 0; k < nseg; ++k)
-        if (cudaMemsetAsync(seg[k], 0, SB, c->stream) != cudaSuccess) {
-            release();
-            return cuda_fail(c, cudaGetLastError(), "clear segment buffer");
-        }
+    int rc = LBM_OK;
+#define LBM_ADJ_CHECK(expr, what)          \
+    do {                                   \
+        cudaError_t e_ = (expr);           \
+        if (e_ != cudaSuccess) {           \
+            rc = cuda_fail(c, e_, what);   \
+            release();                     \
+            return rc;                     \
+        }                                  \
+    } while (0)
+#define LBM_ADJ_ALLOC(ptr, what)                                      \
+    do {                                                              \
+        if (!((ptr) = dev_alloc(c, SB))) {                            \
+            release();                                                \
+            return fail(c, LBM_ERR_OOM, "adjoint: %s (%zu bytes)", what, SB); \
+        }                                                             \
+    } while (0)
 
+    for (int k = 0; k < nseg; ++k) LBM_ADJ_ALLOC(seg[k], "segment state");
+    LBM_ADJ_ALLOC(base, "segment start");
     const void* cf = c->coef();
-    // out-of-place step t -> t+1 from src to dst
     auto step_oop = [&](const void* src, void* dst, long long t) -> cudaError_t {
         c->launches += 1;
         if (c->scheme == LBM_PULL2) return c->ops->step_pull(c->geom, cf, src, dst, c->flag, c->stream);
         return c->ops->step_aa(c->geom, cf, (int)(t & 1), src, dst, c->flag, c->stream);
     };
-    auto layout_at = [&](long long t) { return layout_now(c, t); };
 
-#define LBM_ADJ_CHECK(expr, what)                       \
-    do {                                                \
-        cudaError_t e_ = (expr);                        \
-        if (e_ != cudaSuccess) {                        \
-            rc = cuda_fail(c, e_, what);                \
-            release();                                  \
-            return rc;                                  \
-        }                                               \
-    } while (0)
-
-    // Forward pass from the initial fields: checkpoints at multiples of K.
-    const int init_layout = c->scheme == LBM_PULL2 ? LAYOUT_PULL : LAYOUT_LOCAL;
-    LBM_ADJ_CHECK(c->ops->init(c->geom, cf, init_layout, c->rho_init_null ? nullptr : c->rho_init,
-                               c->u_init_null ? nullptr : c->u_init, stepbuf[0], c->stream),
-                  "adjoint init");
-    c->launches += 1;
-    int sb = 0;
-    for (long long t = 0; t <= n; ++t) {
-        if (t % K == 0 && t < n) {
-            const int k = (int)(t / K);
-            LBM_ADJ_CHECK(cudaMemcpyAsync(ckpt[k], stepbuf[sb], SB, cudaMemcpyDefault, c->stream), "checkpoint copy");
+    if (recorded) {
+        for (int k = 0; k < C; ++k) {
+            ckpt[k] = c->rec_ptr[k];
+            ckpt_host[k] = c->rec_host[k];
         }
-        if (t == n) break;
-        LBM_ADJ_CHECK(step_oop(stepbuf[sb], stepbuf[sb ^ 1], t), "forward recompute");
-        sb ^= 1;
+    } else {
+        // Forward pass from the initial fields, keeping the state at multiples of K.
+        size_t limit = c->opt.adjoint_mem_limit;
+        size_t fr = 0, tot = 0;
+        if (limit == 0) {
+            LBM_ADJ_CHECK(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
+            limit = fr > ((size_t)2 << 30) ? fr - ((size_t)2 << 30) : 0;
+        }
+        for (int k = 0; k < C; ++k) {
+            void* p = nullptr;
+            bool h = false;
+            if ((size_t)(k + 1) * SB <= limit) p = dev_alloc(c, SB);
+            if (!p) {
+                if (cudaMallocHost(&p, SB) != cudaSuccess) {
+                    (void)cudaGetLastError();
+                    release();
+                    return fail(c, LBM_ERR_OOM, "adjoint checkpoint %d", k);
+                }
+                h = true;
+            }
+            ckpt[k] = p;
+            ckpt_host[k] = h;
+            own.push_back(p);
+            own_host.push_back(h);
+        }
+        LBM_ADJ_ALLOC(fwd[0], "forward buffer");
+        LBM_ADJ_ALLOC(fwd[1], "forward buffer");
+        const int init_layout = c->scheme == LBM_PULL2 ? LAYOUT_PULL : LAYOUT_LOCAL;
+        LBM_ADJ_CHECK(cudaMemsetAsync(fwd[0], 0, SB, c->stream), "clear");
+        LBM_ADJ_CHECK(cudaMemsetAsync(fwd[1], 0, SB, c->stream), "clear");
+        LBM_ADJ_CHECK(c->ops->init(c->geom, cf, init_layout, c->rho_init_null ? nullptr : c->rho_init,
+                                   c->u_init_null ? nullptr : c->u_init, fwd[0], c->stream),
+                      "adjoint init");
+        c->launches += 1;
+        int sb = 0;
+        for (long long t = 0; t < n; ++t) {
+            if (t % K == 0)
+                LBM_ADJ_CHECK(cudaMemcpyAsync(ckpt[t / K], fwd[sb], SB, cudaMemcpyDefault, c->stream),
+                              "checkpoint copy");
+            LBM_ADJ_CHECK(step_oop(fwd[sb], fwd[sb ^ 1], t), "forward recompute");
+            sb ^= 1;
+        }
+        dev_free(c, fwd[0], SB);
+        dev_free(c, fwd[1], SB);
+        fwd[0] = fwd[1] = nullptr;
     }
-    // seed from f(n)
+    // solid-cell slots of the recompute buffers are never written; keep them defined
+    for (int k = 0; k < nseg; ++k) LBM_ADJ_CHECK(cudaMemsetAsync(seg[k], 0, SB, c->stream), "clear");
+
+    // Seed from f(n), the context's current state.
     int lc = 0;
-    LBM_ADJ_CHECK(c->ops->adj_seed(c->geom, cf, layout_at(n), stepbuf[sb], loss_grad, c->lam[lc], c->stream),
+    LBM_ADJ_CHECK(c->ops->adj_seed(c->geom, cf, layout_now(c, n), state_ptr(c), loss_grad, c->lam[lc], c->stream),
                   "adjoint seed");
     c->launches += 1;
-    // Reverse sweep over segments.
+    // Reverse sweep over segments: recompute states t0+1 .. t0+len-1, then len adjoint steps.
     for (int s = C - 1; s >= 0; --s) {
         const long long t0 = (long long)s * K;
         const int len = (int)std::min<long long>(K, n - t0);
-        // states t0 .. t0+len-1: state(t0) in stepbuf[0], state(t0+j) in seg[j-1]
-        LBM_ADJ_CHECK(cudaMemcpyAsync(stepbuf[0], ckpt[s], SB, cudaMemcpyDefault, c->stream), "checkpoint restore");
+        const void* start = ckpt[s];
+        if (ckpt_host[s]) {
+            LBM_ADJ_CHECK(cudaMemcpyAsync(base, ckpt[s], SB, cudaMemcpyHostToDevice, c->stream), "checkpoint restore");
+            start = base;
+        }
         for (int j = 1; j < len; ++j) {
-            const void* src = j == 1 ? stepbuf[0] : seg[j - 2];
+            const void* src = j == 1 ? start : seg[j - 2];
             LBM_ADJ_CHECK(step_oop(src, seg[j - 1], t0 + j - 1), "segment recompute");
         }
         for (int j = len - 1; j >= 0; --j) {
-            const void* ft = j == 0 ? stepbuf[0] : seg[j - 1];
-            LBM_ADJ_CHECK(c->ops->adj_step(c->geom, cf, layout_at(t0 + j), ft, c->lam[lc], c->lam[lc ^ 1], c->gpart,
-                                           c->stream),
+            const void* ft = j == 0 ? start : seg[j - 1];
+            LBM_ADJ_CHECK(c->ops->adj_step(c->geom, cf, layout_now(c, t0 + j), ft, c->lam[lc], c->lam[lc ^ 1],
+                                           c->gpart, c->stream),
                           "adjoint step");
             c->launches += 1;
             lc ^= 1;
@@ -794,6 +877,7 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
                   "gradient copy");
     LBM_ADJ_CHECK(cudaStreamSynchronize(c->stream), "adjoint sync");
 #undef LBM_ADJ_CHECK
+#undef LBM_ADJ_ALLOC
     if (c->d == 3) {
         for (int k = 0; k < 6; ++k) c->grad_theta[k] = c->hout[k];
     } else {
@@ -875,6 +959,7 @@ int lbm_set_state(lbm_ctx* c, const void* src, size_t bytes) {
     c->state_valid = true;
     c->init_fields = false;  // the adjoint needs the initial fields of an lbm_init
     c->grads_ready = false;
+    c->rec_valid = 0;
     return LBM_OK;
 }
 

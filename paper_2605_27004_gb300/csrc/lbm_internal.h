@@ -1,18 +1,19 @@
-// Internal interface between the C-ABI host code (lbm_host.cu) and the per-lattice kernel
-// translation units (lbm_d2q9.cu, lbm_d3q19.cu, lbm_d3q27.cu). Not installed, not public.
+// Internal interface between the C-ABI host code (lbm_host.cu) and the kernel translation units
+// (lbm_ops.cu, one object per lattice and storage). Not installed, not public.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace lbm {
 
-// Grid geometry as every kernel sees it.
+// Grid geometry as every kernel sees it. N < 2^31, so in-plane offsets are 32-bit.
 struct Geom {
     int nx, ny, nz;
-    long long N;           // nx*ny*nz
-    const uint32_t* mask;  // bit-packed solid mask (bit x%32 of word x/32 of row y+ny*z), or null
-    int W;                 // mask words per row = ceil(nx/32)
+    uint32_t N;            // nx*ny*nz
+    const uint32_t* link;  // per-cell link words or null (all fluid): bit i set when the
+                           // neighbour x - c_i is solid, bit 31 set when x itself is solid
 };
+constexpr uint32_t LINK_SOLID = 0x80000000u;
 
 // Per-run constants, derived on the host in FP64 from (tau, Theta, rho0, order) and rounded
 // once to the arithmetic type T. Arrays are indexed by the library's direction order.
@@ -61,6 +62,8 @@ struct Ops {
                             void* lam, double* gpart, cudaStream_t);
     cudaError_t (*adj_init)(const Geom&, const void* coef, const void* rho0, const void* u0, const void* lam0,
                             void* du0, double* gpart, cudaStream_t);
+    // link words from a byte mask (device, N bytes, nonzero = solid)
+    cudaError_t (*link_mask)(const Geom&, const uint8_t* solid, uint32_t* link, cudaStream_t);
 };
 
 // One translation unit per (lattice, storage): lbm_ops.cu compiled with LBM_Q / LBM_S.

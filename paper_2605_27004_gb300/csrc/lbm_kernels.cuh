@@ -3,7 +3,9 @@
 // Every kernel runs one thread per lattice cell, x fastest, so that each direction's loads and
 // stores of a warp touch 32 consecutive elements of one structure-of-arrays plane [q][N]
 // (coalesced; the x-1/x+1 shifted reads of a warp straddle one extra 32-byte sector that the
-// neighbouring warp reads anyway, and the y/z-shifted rows are re-read from L2).
+// neighbouring warp reads anyway, and the y/z-shifted rows are re-read from L2). Addresses are a
+// per-direction plane pointer plus a 32-bit in-plane offset built from three wrapped x indices
+// and nine wrapped row offsets, so a gathered load costs one add and one wide multiply-add.
 //
 // Arithmetic is carried in the shifted variables d_i = f_i - r_i with r_i the rest equilibrium
 // feq_i(rho0, 0; Theta), whatever the storage form: this keeps the FP32 sums of the moments and
@@ -16,6 +18,12 @@
 //                                                                                   (= -O_opp)
 //   with drho = rho - rho0, c3 = 9/2 (third order) or 0 (second order).
 // BGK relaxation (Eq. LBE_BGK): d_i <- d_i + (feq_i - r_i - d_i)/tau.
+//
+// FP32 momentum identity: with weights and coefficients rounded to FP32 the discrete first
+// moment of the equilibrium is rho u (1 + eps) with a systematic eps ~ 2e-8, which drifts the
+// momentum by ~1e-5 over 1000 steps. In exact arithmetic BGK conserves momentum, so the FP32
+// storage forms remove the post-collision momentum defect along 3 w_i c_i (a no-op in exact
+// arithmetic; mass and the other moments are untouched since sum_i 3 w_i c_i = 0).
 #pragma once
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -36,28 +44,29 @@ struct Store<0> {
     using type = float;
     using T = float;
     static constexpr bool shifted = false;
+    static constexpr bool fix_momentum = true;
 };
 template <>
 struct Store<1> {
     using type = double;
     using T = double;
     static constexpr bool shifted = false;
+    static constexpr bool fix_momentum = false;
 };
 template <>
 struct Store<2> {
     using type = float;
     using T = float;
     static constexpr bool shifted = true;
+    static constexpr bool fix_momentum = true;
 };
 template <>
 struct Store<3> {
     using type = __half;
     using T = float;
     static constexpr bool shifted = true;
+    static constexpr bool fix_momentum = false;  // FP16 rounding (1e-3) dwarfs the 1e-8 bias
 };
-
-__device__ __forceinline__ float raw_to_T(float v) { return v; }
-__device__ __forceinline__ double raw_to_T(double v) { return v; }
 
 // read-only (non-coherent) loads: used when the source array is not written by the kernel
 __device__ __forceinline__ float ld_ro(const float* p) { return __ldg(p); }
@@ -84,16 +93,29 @@ __device__ __forceinline__ typename Store<S>::T from_shifted(typename Store<S>::
     return Store<S>::shifted ? d : d + r;
 }
 
+// Base pointers of the q planes of a structure-of-arrays buffer, passed by value as a kernel
+// parameter so that the bases stay in the constant bank instead of occupying registers.
+template <typename P>
+struct Planes {
+    P* p[27];
+};
+template <typename P>
+Planes<P> planes_of(P* base, int q, uint32_t N) {
+    Planes<P> r{};
+    for (int i = 0; i < q; ++i) r.p[i] = base ? base + (size_t)i * N : nullptr;
+    return r;
+}
+
 // ---------------------------------------------------------------------------------------------
-// Cell addressing with periodic wrap. X[k] = x - (k - 1) and RW[ky][kz] = (y - (ky - 1)) +
-// ny (z - (kz - 1)), all wrapped, so the index of x - c is X[c.x + 1] + nx RW[c.y + 1][c.z + 1]
-// and the index of x + c is X[1 - c.x] + nx RW[1 - c.y][1 - c.z].
+// Cell addressing with periodic wrap: X[k] = x - (k - 1), R[a][b] = nx ((y - (a - 1)) +
+// ny (z - (b - 1))), all wrapped. Offset of x - c: X[c.x + 1] + R[c.y + 1][c.z + 1];
+// offset of x + c: X[1 - c.x] + R[1 - c.y][1 - c.z].
 // ---------------------------------------------------------------------------------------------
 struct Cell {
     int x, y, z;
-    long long n;
-    int X[3];
-    long long RW[3][3];
+    uint32_t n;
+    uint32_t X[3];
+    uint32_t R[3][3];
 };
 
 __device__ __forceinline__ bool make_cell(const Geom& g, Cell& c) {
@@ -101,54 +123,51 @@ __device__ __forceinline__ bool make_cell(const Geom& g, Cell& c) {
     c.y = blockIdx.y * blockDim.y + threadIdx.y;
     c.z = blockIdx.z;
     if (c.x >= g.nx || c.y >= g.ny) return false;
-    const int yy[3] = {c.y + 1 == g.ny ? 0 : c.y + 1, c.y, c.y == 0 ? g.ny - 1 : c.y - 1};
-    const int zz[3] = {c.z + 1 == g.nz ? 0 : c.z + 1, c.z, c.z == 0 ? g.nz - 1 : c.z - 1};
-    c.X[0] = c.x + 1 == g.nx ? 0 : c.x + 1;
-    c.X[1] = c.x;
-    c.X[2] = c.x == 0 ? g.nx - 1 : c.x - 1;
+    const uint32_t yy[3] = {(uint32_t)(c.y + 1 == g.ny ? 0 : c.y + 1), (uint32_t)c.y,
+                            (uint32_t)(c.y == 0 ? g.ny - 1 : c.y - 1)};
+    const uint32_t zz[3] = {(uint32_t)(c.z + 1 == g.nz ? 0 : c.z + 1), (uint32_t)c.z,
+                            (uint32_t)(c.z == 0 ? g.nz - 1 : c.z - 1)};
+    c.X[0] = c.x + 1 == g.nx ? 0u : (uint32_t)(c.x + 1);
+    c.X[1] = (uint32_t)c.x;
+    c.X[2] = c.x == 0 ? (uint32_t)(g.nx - 1) : (uint32_t)(c.x - 1);
+    const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) c.RW[a][b] = (long long)yy[a] + (long long)g.ny * zz[b];
-    c.n = (long long)c.x + (long long)g.nx * c.RW[1][1];
+        for (int b = 0; b < 3; ++b) c.R[a][b] = nx * (yy[a] + ny * zz[b]);
+    c.n = c.X[1] + c.R[1][1];
     return true;
 }
 
-__device__ __forceinline__ long long idx_minus(const Geom& g, const Cell& c, Vec3 v) {
-    return (long long)c.X[v.x + 1] + (long long)g.nx * c.RW[v.y + 1][v.z + 1];
+__device__ __forceinline__ uint32_t off_minus(const Cell& c, Vec3 v) { return c.X[v.x + 1] + c.R[v.y + 1][v.z + 1]; }
+__device__ __forceinline__ uint32_t off_plus(const Cell& c, Vec3 v) { return c.X[1 - v.x] + c.R[1 - v.y][1 - v.z]; }
+
+template <bool MASK>
+__device__ __forceinline__ uint32_t link_of(const Geom& g, const Cell& c) {
+    return MASK ? __ldg(g.link + c.n) : 0u;
 }
-__device__ __forceinline__ long long idx_plus(const Geom& g, const Cell& c, Vec3 v) {
-    return (long long)c.X[1 - v.x] + (long long)g.nx * c.RW[1 - v.y][1 - v.z];
-}
-__device__ __forceinline__ bool solid_bit(const Geom& g, int xx, long long row) {
-    return (__ldg(g.mask + row * g.W + (xx >> 5)) >> (xx & 31)) & 1u;
-}
-__device__ __forceinline__ bool solid_minus(const Geom& g, const Cell& c, Vec3 v) {
-    return solid_bit(g, c.X[v.x + 1], c.RW[v.y + 1][v.z + 1]);
-}
-__device__ __forceinline__ bool solid_plus(const Geom& g, const Cell& c, Vec3 v) {
-    return solid_bit(g, c.X[1 - v.x], c.RW[1 - v.y][1 - v.z]);
-}
-__device__ __forceinline__ bool solid_self(const Geom& g, const Cell& c) { return solid_bit(g, c.x, c.RW[1][1]); }
+__device__ __forceinline__ bool link_bit(uint32_t lw, int i) { return (lw >> i) & 1u; }
 
 // Gather of the pre-collision populations of one cell in shifted form (see Layout).
 template <int Q, int S, bool MASK, int LAYOUT, bool RO>
-__device__ __forceinline__ void gather(const Geom& g, const Cell& c, const Coef<typename Store<S>::T>& cf,
-                                       const typename Store<S>::type* src, typename Store<S>::T (&d)[Q]) {
-    const long long N = g.N;
+__device__ __forceinline__ void gather(const Cell& c, uint32_t lw, const Coef<typename Store<S>::T>& cf,
+                                       const Planes<const typename Store<S>::type>& src,
+                                       typename Store<S>::T (&d)[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const Vec3 v = vel<Q>(i);
-        long long at;
+        const typename Store<S>::type* p;
         if (LAYOUT == LAYOUT_LOCAL || i == 0) {
-            at = (long long)i * N + c.n;
+            p = src.p[i] + c.n;
         } else {
-            const bool wall = MASK && solid_minus(g, c, v);
-            const int slot_n = LAYOUT == LAYOUT_PULL ? i : opp(i);   // slot read from the neighbour
-            const int slot_w = LAYOUT == LAYOUT_PULL ? opp(i) : i;   // slot read on a wall link
-            at = wall ? (long long)slot_w * N + c.n : (long long)slot_n * N + idx_minus(g, c, v);
+            const int slot_n = LAYOUT == LAYOUT_PULL ? i : opp(i);  // slot read from the neighbour
+            const int slot_w = LAYOUT == LAYOUT_PULL ? opp(i) : i;  // slot read on a wall link
+            if (MASK && link_bit(lw, i))
+                p = src.p[slot_w] + c.n;
+            else
+                p = src.p[slot_n] + off_minus(c, v);
         }
-        const auto raw = RO ? ld_ro(src + at) : ld_rw(src + at);
+        const auto raw = RO ? ld_ro(p) : ld_rw(p);
         d[i] = to_shifted<S>(raw, cf.r[i]);
     }
 }
@@ -158,29 +177,34 @@ __device__ __forceinline__ void gather(const Geom& g, const Cell& c, const Coef<
 // ---------------------------------------------------------------------------------------------
 template <typename T>
 struct Macro {
-    T drho, rho, ux, uy, uz;
+    T drho, rho, jx, jy, jz, ux, uy, uz;
 };
+
+template <typename T>
+__device__ __forceinline__ void add_c(Vec3 v, T val, T& x, T& y, T& z) {
+    if (v.x == 1) x += val;
+    if (v.x == -1) x -= val;
+    if (v.y == 1) y += val;
+    if (v.y == -1) y -= val;
+    if (v.z == 1) z += val;
+    if (v.z == -1) z -= val;
+}
 
 template <int Q, typename T>
 __device__ __forceinline__ Macro<T> macro_of(const T (&d)[Q], T rho0) {
-    constexpr int P = Lat<Q>::P;
     T s = d[0], jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-        const Vec3 v = vel<Q>(2 * k + 1);
+    for (int k = 0; k < Lat<Q>::P; ++k) {
         const T a = d[2 * k + 1], b = d[2 * k + 2];
         s += a + b;
-        const T df = a - b;
-        if (v.x == 1) jx += df;
-        if (v.x == -1) jx -= df;
-        if (v.y == 1) jy += df;
-        if (v.y == -1) jy -= df;
-        if (v.z == 1) jz += df;
-        if (v.z == -1) jz -= df;
+        add_c<T>(vel<Q>(2 * k + 1), a - b, jx, jy, jz);
     }
     Macro<T> m;
     m.drho = s;
     m.rho = rho0 + s;
+    m.jx = jx;
+    m.jy = jy;
+    m.jz = jz;
     const T inv = T(1) / m.rho;
     m.ux = jx * inv;
     m.uy = jy * inv;
@@ -188,8 +212,9 @@ __device__ __forceinline__ Macro<T> macro_of(const T (&d)[Q], T rho0) {
     return m;
 }
 
+// v . (ax, ay, az) for a lattice vector with components in {-1, 0, 1}
 template <typename T>
-__device__ __forceinline__ T dotv(Vec3 v, T ax, T ay, T az) {
+__device__ __forceinline__ T vdot(Vec3 v, T ax, T ay, T az) {
     T r = T(0);
     if (v.x == 1) r += ax;
     if (v.x == -1) r -= ax;
@@ -228,8 +253,8 @@ __device__ __forceinline__ void pair_eq(const Coef<T>& cf, const EqCell<T>& e, i
     const int i = 2 * k + 1;
     const Vec3 v = vel<Q>(i);
     const T w = T(weight<Q>(i));
-    uc = dotv<T>(v, e.ux, e.uy, e.uz);
-    const T qk = dotv<T>(v, e.kx, e.ky, e.kz);
+    uc = vdot<T>(v, e.ux, e.uy, e.uz);
+    const T qk = vdot<T>(v, e.kx, e.ky, e.kz);
     E = e.drho * cf.A[i] + w * e.r45 * (uc * uc - e.usq * T(1.0 / 3.0));
     O = e.rho * (uc * cf.B[i] + w * cf.c3 * (uc * (uc * uc - e.usq) - T(2) * qk));
 }
@@ -240,7 +265,7 @@ __device__ __forceinline__ T rest_eq(const Coef<T>& cf, const EqCell<T>& e) {
 }
 
 // BGK collision in place on shifted populations; returns the macroscopic state.
-template <int Q, typename T>
+template <int Q, typename T, bool FIX>
 __device__ __forceinline__ Macro<T> bgk(const Coef<T>& cf, T (&d)[Q]) {
     const Macro<T> m = macro_of<Q, T>(d, cf.rho0);
     const EqCell<T> e = eq_cell<T>(cf, m.drho, m.rho, m.ux, m.uy, m.uz);
@@ -252,6 +277,19 @@ __device__ __forceinline__ Macro<T> bgk(const Coef<T>& cf, T (&d)[Q]) {
         pair_eq<Q, T>(cf, e, k, E, O, uc);
         d[2 * k + 1] = om1 * d[2 * k + 1] + om * (E + O);
         d[2 * k + 2] = om1 * d[2 * k + 2] + om * (E - O);
+    }
+    if (FIX) {
+        // post-collision momentum defect, removed along 3 w_i c_i
+        T ex = -m.jx, ey = -m.jy, ez = -m.jz;
+#pragma unroll
+        for (int k = 0; k < Lat<Q>::P; ++k) add_c<T>(vel<Q>(2 * k + 1), d[2 * k + 1] - d[2 * k + 2], ex, ey, ez);
+#pragma unroll
+        for (int k = 0; k < Lat<Q>::P; ++k) {
+            const Vec3 v = vel<Q>(2 * k + 1);
+            const T corr = T(3.0 * weight<Q>(2 * k + 1)) * vdot<T>(v, ex, ey, ez);
+            d[2 * k + 1] -= corr;
+            d[2 * k + 2] += corr;
+        }
     }
     return m;
 }
@@ -267,18 +305,19 @@ __device__ __forceinline__ bool bad_cell(const Macro<T>& m) {
 // ---------------------------------------------------------------------------------------------
 template <int Q, int S, bool MASK>
 __global__ void __launch_bounds__(256) k_step_pull(Geom g, Coef<typename Store<S>::T> cf,
-                                                   const typename Store<S>::type* __restrict__ src,
-                                                   typename Store<S>::type* __restrict__ dst, int* __restrict__ flag) {
+                                                   const Planes<const typename Store<S>::type> src,
+                                                   const Planes<typename Store<S>::type> dst, int* __restrict__ flag) {
     using T = typename Store<S>::T;
     Cell c;
     if (!make_cell(g, c)) return;
-    if (MASK && solid_self(g, c)) return;
+    const uint32_t lw = link_of<MASK>(g, c);
+    if (MASK && (lw & LINK_SOLID)) return;
     T d[Q];
-    gather<Q, S, MASK, LAYOUT_PULL, true>(g, c, cf, src, d);
-    const Macro<T> m = bgk<Q, T>(cf, d);
+    gather<Q, S, MASK, LAYOUT_PULL, true>(c, lw, cf, src, d);
+    const Macro<T> m = bgk<Q, T, Store<S>::fix_momentum>(cf, d);
     if (bad_cell(m)) *flag = 1;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st_raw(dst + (long long)i * g.N + c.n, from_shifted<S>(d[i], cf.r[i]));
+    for (int i = 0; i < Q; ++i) st_raw(dst.p[i] + c.n, from_shifted<S>(d[i], cf.r[i]));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -286,37 +325,40 @@ __global__ void __launch_bounds__(256) k_step_pull(Geom g, Coef<typename Store<S
 //   even: read A[i][x], write f*_i to A[opp i][x]                     (state LOCAL -> AAODD)
 //   odd:  read f_i per AAODD, write f*_i to A[i][x + c_i], or to A[opp i][x] if x + c_i is
 //         solid                                                         (state AAODD -> LOCAL)
-// Each thread writes exactly the slots it read, so the in-place update is race free.
+// Each thread writes exactly the slots it read, so the in-place update is race free. The link
+// bit of x + c_i is the bit of direction opp(i).
 // ---------------------------------------------------------------------------------------------
 template <int Q, int S, bool MASK, int ODD>
 __global__ void __launch_bounds__(256) k_step_aa(Geom g, Coef<typename Store<S>::T> cf,
-                                                 const typename Store<S>::type* src, typename Store<S>::type* dst,
-                                                 int* __restrict__ flag) {
+                                                 const Planes<const typename Store<S>::type> src,
+                                                 const Planes<typename Store<S>::type> dst, int* __restrict__ flag) {
     using T = typename Store<S>::T;
     Cell c;
     if (!make_cell(g, c)) return;
-    if (MASK && solid_self(g, c)) return;
+    const uint32_t lw = link_of<MASK>(g, c);
+    if (MASK && (lw & LINK_SOLID)) return;
     T d[Q];
     if (ODD)
-        gather<Q, S, MASK, LAYOUT_AAODD, false>(g, c, cf, src, d);
+        gather<Q, S, MASK, LAYOUT_AAODD, false>(c, lw, cf, src, d);
     else
-        gather<Q, S, MASK, LAYOUT_LOCAL, false>(g, c, cf, src, d);
-    const Macro<T> m = bgk<Q, T>(cf, d);
+        gather<Q, S, MASK, LAYOUT_LOCAL, false>(c, lw, cf, src, d);
+    const Macro<T> m = bgk<Q, T, Store<S>::fix_momentum>(cf, d);
     if (bad_cell(m)) *flag = 1;
-    const long long N = g.N;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        long long at;
+        typename Store<S>::type* p;
         if (i == 0) {
-            at = c.n;
+            p = dst.p[0] + c.n;
         } else if (!ODD) {
-            at = (long long)opp(i) * N + c.n;
+            p = dst.p[opp(i)] + c.n;
         } else {
             const Vec3 v = vel<Q>(i);
-            const bool wall = MASK && solid_plus(g, c, v);
-            at = wall ? (long long)opp(i) * N + c.n : (long long)i * N + idx_plus(g, c, v);
+            if (MASK && link_bit(lw, opp(i)))
+                p = dst.p[opp(i)] + c.n;
+            else
+                p = dst.p[i] + off_plus(c, v);
         }
-        st_raw(dst + at, from_shifted<S>(d[i], cf.r[i]));
+        st_raw(p, from_shifted<S>(d[i], cf.r[i]));
     }
 }
 
@@ -327,16 +369,17 @@ template <int Q, int S, bool MASK, int LAYOUT>
 __global__ void __launch_bounds__(256) k_init(Geom g, Coef<typename Store<S>::T> cf,
                                               const typename Store<S>::T* __restrict__ rho_in,
                                               const typename Store<S>::T* __restrict__ u_in,
-                                              typename Store<S>::type* __restrict__ dst) {
+                                              const Planes<typename Store<S>::type> dst) {
     using T = typename Store<S>::T;
     Cell c;
     if (!make_cell(g, c)) return;
-    if (MASK && solid_self(g, c)) return;
-    const long long N = g.N;
+    const uint32_t lw = link_of<MASK>(g, c);
+    if (MASK && (lw & LINK_SOLID)) return;
+    const uint32_t N = g.N;
     const T rho = rho_in ? rho_in[c.n] : cf.rho0;
     const T ux = u_in ? u_in[c.n] : T(0);
     const T uy = u_in ? u_in[N + c.n] : T(0);
-    const T uz = (u_in && Lat<Q>::D == 3) ? u_in[2 * N + c.n] : T(0);
+    const T uz = (u_in && Lat<Q>::D == 3) ? u_in[2 * (size_t)N + c.n] : T(0);
     const EqCell<T> e = eq_cell<T>(cf, rho - cf.rho0, rho, ux, uy, uz);
     T d[Q];
     d[0] = rest_eq<Q, T>(cf, e);
@@ -349,62 +392,75 @@ __global__ void __launch_bounds__(256) k_init(Geom g, Coef<typename Store<S>::T>
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        long long at;
+        typename Store<S>::type* p;
         if (LAYOUT == LAYOUT_LOCAL || i == 0) {
-            at = (long long)i * N + c.n;
+            p = dst.p[i] + c.n;
         } else {
             // the slot the PULL gather reads f_i(x) from
-            const Vec3 v = vel<Q>(i);
-            const bool wall = MASK && solid_minus(g, c, v);
-            at = wall ? (long long)opp(i) * N + c.n : (long long)i * N + idx_minus(g, c, v);
+            if (MASK && link_bit(lw, i))
+                p = dst.p[opp(i)] + c.n;
+            else
+                p = dst.p[i] + off_minus(c, vel<Q>(i));
         }
-        st_raw(dst + at, from_shifted<S>(d[i], cf.r[i]));
+        st_raw(p, from_shifted<S>(d[i], cf.r[i]));
     }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Link words from a byte mask: bit i = solid(x - c_i), bit 31 = solid(x).
+// ---------------------------------------------------------------------------------------------
+template <int Q>
+__global__ void __launch_bounds__(256) k_link_mask(Geom g, const uint8_t* __restrict__ solid,
+                                                   uint32_t* __restrict__ link) {
+    Cell c;
+    if (!make_cell(g, c)) return;
+    uint32_t lw = solid[c.n] ? LINK_SOLID : 0u;
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+        if (solid[off_minus(c, vel<Q>(i))]) lw |= 1u << i;
+    link[c.n] = lw;
 }
 
 // ---------------------------------------------------------------------------------------------
 // Observables of f(t): rho, u, Pi (Eqs. a0discrete_f, a1discrete_f; Appendix E second moment),
 // and optionally the unshifted populations f_i in direction order.
 // ---------------------------------------------------------------------------------------------
-template <int D>
-struct PiIdx;
-template <>
-struct PiIdx<2> {
-    static constexpr int n = 3;
-};
-template <>
-struct PiIdx<3> {
-    static constexpr int n = 6;
-};
-__host__ __device__ constexpr int pi_a(int D, int k) { return D == 2 ? (k == 0 ? 0 : k == 1 ? 1 : 0) : (k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 2 : k == 3 ? 0 : k == 4 ? 0 : 1); }
-__host__ __device__ constexpr int pi_b(int D, int k) { return D == 2 ? (k == 0 ? 0 : k == 1 ? 1 : 1) : (k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 2 : k == 3 ? 1 : k == 4 ? 2 : 2); }
-__host__ __device__ constexpr int pi_full(int D, int k) { return D == 2 ? (k == 2 ? 3 : k) : k; }  // index into K[6]-style xx,yy,zz,xy,xz,yz
+__host__ __device__ constexpr int pi_a(int D, int k) {
+    return D == 2 ? (k == 0 ? 0 : k == 1 ? 1 : 0) : (k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 2 : k == 3 ? 0 : k == 4 ? 0 : 1);
+}
+__host__ __device__ constexpr int pi_b(int D, int k) {
+    return D == 2 ? (k == 0 ? 0 : k == 1 ? 1 : 1) : (k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 2 : k == 3 ? 1 : k == 4 ? 2 : 2);
+}
+// index into the xx, yy, zz, xy, xz, yz ordering of Coef::Pirest
+__host__ __device__ constexpr int pi_full(int D, int k) { return D == 2 ? (k == 2 ? 3 : k) : k; }
 __host__ __device__ constexpr int comp(Vec3 v, int a) { return a == 0 ? v.x : a == 1 ? v.y : v.z; }
 
 template <int Q, int S, bool MASK, int LAYOUT>
 __global__ void __launch_bounds__(256) k_moments(Geom g, Coef<typename Store<S>::T> cf,
-                                                 const typename Store<S>::type* __restrict__ src,
+                                                 const Planes<const typename Store<S>::type> src,
                                                  typename Store<S>::T* __restrict__ rho_out,
                                                  typename Store<S>::T* __restrict__ u_out,
                                                  typename Store<S>::T* __restrict__ pi_out,
                                                  typename Store<S>::T* __restrict__ f_out) {
     using T = typename Store<S>::T;
     constexpr int D = Lat<Q>::D;
+    constexpr int NP = D == 2 ? 3 : 6;
     Cell c;
     if (!make_cell(g, c)) return;
-    const long long N = g.N;
-    if (MASK && solid_self(g, c)) {
+    const size_t N = g.N;
+    const uint32_t lw = link_of<MASK>(g, c);
+    if (MASK && (lw & LINK_SOLID)) {
         if (rho_out) rho_out[c.n] = T(0);
         if (u_out)
             for (int a = 0; a < D; ++a) u_out[a * N + c.n] = T(0);
         if (pi_out)
-            for (int k = 0; k < PiIdx<D>::n; ++k) pi_out[k * N + c.n] = T(0);
+            for (int k = 0; k < NP; ++k) pi_out[k * N + c.n] = T(0);
         if (f_out)
             for (int i = 0; i < Q; ++i) f_out[i * N + c.n] = T(0);
         return;
     }
     T d[Q];
-    gather<Q, S, MASK, LAYOUT, true>(g, c, cf, src, d);
+    gather<Q, S, MASK, LAYOUT, true>(c, lw, cf, src, d);
     const Macro<T> m = macro_of<Q, T>(d, cf.rho0);
     if (rho_out) rho_out[c.n] = m.rho;
     if (u_out) {
@@ -414,7 +470,7 @@ __global__ void __launch_bounds__(256) k_moments(Geom g, Coef<typename Store<S>:
     }
     if (pi_out) {
 #pragma unroll
-        for (int k = 0; k < PiIdx<D>::n; ++k) {
+        for (int k = 0; k < NP; ++k) {
             T s = T(0);
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
@@ -432,60 +488,64 @@ __global__ void __launch_bounds__(256) k_moments(Geom g, Coef<typename Store<S>:
 }
 
 // ---------------------------------------------------------------------------------------------
-// Block-level FP64 reduction of W values per thread into rec[W] (thread 0 holds the result).
+// Block reductions. Thread 0 of the block ends with the sums.
+// FP64 throughout for totals; for gradient records the 32 lanes of a warp are summed in the
+// arithmetic type first, then the warps and all later accumulation are FP64.
 // ---------------------------------------------------------------------------------------------
-template <int W>
-__device__ __forceinline__ void block_sum(double (&v)[W], double (&out)[W]) {
+__device__ __forceinline__ long long block_linear() {
+    return (long long)blockIdx.x + (long long)gridDim.x * ((long long)blockIdx.y + (long long)gridDim.y * blockIdx.z);
+}
+
+template <int W, typename T>
+__device__ __forceinline__ void block_sum_to_double(T (&v)[W], double (&out)[W]) {
     __shared__ double sh[8][W];
-    const int lane = (threadIdx.x + threadIdx.y * blockDim.x) & 31;
-    const int warp = (threadIdx.x + threadIdx.y * blockDim.x) >> 5;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-        double s = v[k];
+        T s = v[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         v[k] = s;
     }
     if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < W; ++k) sh[warp][k] = v[k];
+        for (int k = 0; k < W; ++k) sh[warp][k] = (double)v[k];
     __syncthreads();
-    if (warp == 0) {
+    if (tid == 0) {
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-            double s = lane < nwarps ? sh[lane][k] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            double s = 0.0;
+            for (int w = 0; w < nwarps; ++w) s += sh[w][k];
             out[k] = s;
         }
     }
 }
 
-__device__ __forceinline__ long long block_linear() {
-    return (long long)blockIdx.x + (long long)gridDim.x * ((long long)blockIdx.y + (long long)gridDim.y * blockIdx.z);
-}
-
 // Totals over fluid cells: partial[block][0] = sum rho, [1..3] = sum j, in FP64.
 template <int Q, int S, bool MASK, int LAYOUT>
 __global__ void __launch_bounds__(256) k_totals(Geom g, Coef<typename Store<S>::T> cf,
-                                                const typename Store<S>::type* __restrict__ src,
+                                                const Planes<const typename Store<S>::type> src,
                                                 double* __restrict__ partials, int* __restrict__ flag) {
     using T = typename Store<S>::T;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     Cell c;
-    if (make_cell(g, c) && !(MASK && solid_self(g, c))) {
-        T d[Q];
-        gather<Q, S, MASK, LAYOUT, true>(g, c, cf, src, d);
-        const Macro<T> m = macro_of<Q, T>(d, cf.rho0);
-        if (bad_cell(m)) *flag = 1;
-        v[0] = (double)m.rho;
-        v[1] = (double)m.rho * (double)m.ux;
-        v[2] = (double)m.rho * (double)m.uy;
-        v[3] = (double)m.rho * (double)m.uz;
+    if (make_cell(g, c)) {
+        const uint32_t lw = link_of<MASK>(g, c);
+        if (!(MASK && (lw & LINK_SOLID))) {
+            T d[Q];
+            gather<Q, S, MASK, LAYOUT, true>(c, lw, cf, src, d);
+            const Macro<T> m = macro_of<Q, T>(d, cf.rho0);
+            if (bad_cell(m)) *flag = 1;
+            v[0] = (double)m.rho;
+            v[1] = (double)m.jx;
+            v[2] = (double)m.jy;
+            v[3] = (double)m.jz;
+        }
     }
     double out[4];
-    block_sum<4>(v, out);
+    block_sum_to_double<4, double>(v, out);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         const long long b = block_linear();
 #pragma unroll
@@ -511,16 +571,15 @@ __global__ void __launch_bounds__(256) k_totals(Geom g, Coef<typename Store<S>::
 // ---------------------------------------------------------------------------------------------
 template <typename T>
 struct AdjAcc {
-    T v0, B, P0, Q0;
+    T v0, B, P0, Q0, gE;  // gE = sum_i mu_i (feq_i - r_i)
     T Va[3], V[3];
     T P[6], Qm[6];  // xx yy zz xy xz yz
 };
 
 template <int Q, typename T>
-__device__ __forceinline__ AdjAcc<T> adj_accumulate(const Coef<T>& cf, const EqCell<T>& e, const T (&mu)[Q],
-                                                    T* gtau_part, const T* d) {
+__device__ __forceinline__ AdjAcc<T> adj_accumulate(const Coef<T>& cf, const EqCell<T>& e, const T (&mu)[Q]) {
     AdjAcc<T> A;
-    A.v0 = A.B = A.P0 = A.Q0 = T(0);
+    A.v0 = A.B = A.P0 = A.Q0 = A.gE = T(0);
 #pragma unroll
     for (int a = 0; a < 3; ++a) A.Va[a] = A.V[a] = T(0);
 #pragma unroll
@@ -533,7 +592,7 @@ __device__ __forceinline__ AdjAcc<T> adj_accumulate(const Coef<T>& cf, const EqC
         A.P0 += m;
         A.B += T(3) * m;
         A.v0 += m * (T(1) + T(4.5) * cf.h[0] + T(1.5) * usq);
-        if (gtau_part) *gtau_part += mu[0] * (rest_eq<Q, T>(cf, e) - d[0]);
+        A.gE += mu[0] * rest_eq<Q, T>(cf, e);
     }
 #pragma unroll
     for (int k = 0; k < Lat<Q>::P; ++k) {
@@ -542,22 +601,18 @@ __device__ __forceinline__ AdjAcc<T> adj_accumulate(const Coef<T>& cf, const EqC
         const T w = T(weight<Q>(i));
         T E, O, uc;
         pair_eq<Q, T>(cf, e, k, E, O, uc);
-        const T sm = w * (mu[i] + mu[i + 1]);
-        const T dm = w * (mu[i] - mu[i + 1]);
+        const T ms = mu[i] + mu[i + 1], md = mu[i] - mu[i + 1];
+        const T sm = w * ms;
+        const T dm = w * md;
         const T uc2 = uc * uc;
+        A.gE += E * ms + O * md;
         A.P0 += sm;
         A.Q0 += uc * dm;
         A.B += T(3) * sm + T(2) * c3 * uc * dm;
         A.v0 += sm * (T(1) + T(4.5) * cf.h[i] - T(4.5) * uc2 + T(1.5) * usq) - T(2) * c3 * uc * (uc2 - usq) * dm;
         const T al = (T(3) + c3 * (T(3) * uc2 - usq + T(3) * cf.h[i])) * dm + T(9) * uc * sm;
-        const T cc[3] = {T(v.x), T(v.y), T(v.z)};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (comp(v, a) != 0) {
-                A.Va[a] += cc[a] * al;
-                A.V[a] += cc[a] * dm;
-            }
-        }
+        add_c<T>(v, al, A.Va[0], A.Va[1], A.Va[2]);
+        add_c<T>(v, dm, A.V[0], A.V[1], A.V[2]);
 #pragma unroll
         for (int p = 0; p < 6; ++p) {
             const int ca = comp(v, p < 3 ? p : (p == 5 ? 1 : 0));
@@ -571,7 +626,6 @@ __device__ __forceinline__ AdjAcc<T> adj_accumulate(const Coef<T>& cf, const EqC
                 A.Qm[p] -= uc * dm;
             }
         }
-        if (gtau_part) *gtau_part += mu[i] * (E + O - d[i]) + mu[i + 1] * (E - O - d[i + 1]);
     }
     return A;
 }
@@ -599,9 +653,10 @@ __device__ __forceinline__ void adj_finish(const Coef<T>& cf, const EqCell<T>& e
 }
 
 // Gradient record per block: [0..5] Theta (xx yy zz xy xz yz), [6] tau, [7] unused.
-__device__ __forceinline__ void accumulate_record(double (&v)[8], double* gpart) {
+template <typename T>
+__device__ __forceinline__ void accumulate_record(T (&v)[8], double* gpart) {
     double out[8];
-    block_sum<8>(v, out);
+    block_sum_to_double<8, T>(v, out);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         const long long b = block_linear();
 #pragma unroll
@@ -611,79 +666,86 @@ __device__ __forceinline__ void accumulate_record(double (&v)[8], double* gpart)
 
 template <int Q, int S, bool MASK, int LAYOUT>
 __global__ void __launch_bounds__(256) k_adj_seed(Geom g, Coef<typename Store<S>::T> cf,
-                                                  const typename Store<S>::type* __restrict__ src,
+                                                  const Planes<const typename Store<S>::type> src,
                                                   const typename Store<S>::T* __restrict__ grad,
-                                                  typename Store<S>::T* __restrict__ lam) {
+                                                  const Planes<typename Store<S>::T> lam) {
     using T = typename Store<S>::T;
     Cell c;
     if (!make_cell(g, c)) return;
-    if (MASK && solid_self(g, c)) return;
-    const long long N = g.N;
+    const uint32_t lw = link_of<MASK>(g, c);
+    if (MASK && (lw & LINK_SOLID)) return;
+    const size_t N = g.N;
     T d[Q];
-    gather<Q, S, MASK, LAYOUT, true>(g, c, cf, src, d);
+    gather<Q, S, MASK, LAYOUT, true>(c, lw, cf, src, d);
     const Macro<T> m = macro_of<Q, T>(d, cf.rho0);
     const T gx = grad[c.n], gy = grad[N + c.n], gz = Lat<Q>::D == 3 ? grad[2 * N + c.n] : T(0);
     const T inv = T(1) / m.rho;
     const T gu = gx * m.ux + gy * m.uy + gz * m.uz;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) lam[i * N + c.n] = (dotv<T>(vel<Q>(i), gx, gy, gz) - gu) * inv;
+    for (int i = 0; i < Q; ++i) lam.p[i][c.n] = (vdot<T>(vel<Q>(i), gx, gy, gz) - gu) * inv;
 }
 
 template <int Q, int S, bool MASK, int LAYOUT>
 __global__ void __launch_bounds__(256) k_adj_step(Geom g, Coef<typename Store<S>::T> cf,
-                                                  const typename Store<S>::type* __restrict__ src,
-                                                  const typename Store<S>::T* __restrict__ lam_next,
-                                                  typename Store<S>::T* __restrict__ lam, double* __restrict__ gpart) {
+                                                  const Planes<const typename Store<S>::type> src,
+                                                  const Planes<const typename Store<S>::T> lam_next,
+                                                  const Planes<typename Store<S>::T> lam, double* __restrict__ gpart) {
     using T = typename Store<S>::T;
-    double rec[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    T rec[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
     Cell c;
-    if (make_cell(g, c) && !(MASK && solid_self(g, c))) {
-        const long long N = g.N;
-        T d[Q];
-        gather<Q, S, MASK, LAYOUT, true>(g, c, cf, src, d);
-        T mu[Q];
+    if (make_cell(g, c)) {
+        const uint32_t lw = link_of<MASK>(g, c);
+        if (!(MASK && (lw & LINK_SOLID))) {
+            // mu = S^T lambda_{t+1}: reverse gather along +c_i
+            T mu[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if (i == 0) {
-                mu[0] = lam_next[c.n];
-            } else {
-                const Vec3 v = vel<Q>(i);
-                const bool wall = MASK && solid_plus(g, c, v);
-                mu[i] = wall ? lam_next[(long long)opp(i) * N + c.n] : lam_next[(long long)i * N + idx_plus(g, c, v)];
+            for (int i = 0; i < Q; ++i) {
+                const T* p;
+                if (i == 0)
+                    p = lam_next.p[0] + c.n;
+                else if (MASK && link_bit(lw, opp(i)))
+                    p = lam_next.p[opp(i)] + c.n;
+                else
+                    p = lam_next.p[i] + off_plus(c, vel<Q>(i));
+                mu[i] = __ldg(p);
             }
-        }
-        const Macro<T> m = macro_of<Q, T>(d, cf.rho0);
-        const EqCell<T> e = eq_cell<T>(cf, m.drho, m.rho, m.ux, m.uy, m.uz);
-        T gt = T(0);
-        const AdjAcc<T> A = adj_accumulate<Q, T>(cf, e, mu, &gt, d);
-        T v[3], G[6];
-        adj_finish<Q, T>(cf, e, A, v, G);
-        const T om = cf.omega, om1 = T(1) - cf.omega;
-        lam[c.n] = om1 * mu[0] + om * A.v0;
+            // f_t: moments and sum_i mu_i (f_i - r_i), without keeping the populations
+            T dk[Q];
+            gather<Q, S, MASK, LAYOUT, true>(c, lw, cf, src, dk);
+            T smd = T(0);
 #pragma unroll
-        for (int k = 0; k < Lat<Q>::P; ++k) {
-            const int i = 2 * k + 1;
-            const T cv = dotv<T>(vel<Q>(i), v[0], v[1], v[2]);
-            lam[(long long)i * N + c.n] = om1 * mu[i] + om * (A.v0 + cv);
-            lam[(long long)(i + 1) * N + c.n] = om1 * mu[i + 1] + om * (A.v0 - cv);
-        }
+            for (int i = 0; i < Q; ++i) smd += mu[i] * dk[i];
+            const Macro<T> m = macro_of<Q, T>(dk, cf.rho0);
+            const EqCell<T> e = eq_cell<T>(cf, m.drho, m.rho, m.ux, m.uy, m.uz);
+            const AdjAcc<T> A = adj_accumulate<Q, T>(cf, e, mu);
+            T v[3], G[6];
+            adj_finish<Q, T>(cf, e, A, v, G);
+            const T om = cf.omega, om1 = T(1) - cf.omega;
+            lam.p[0][c.n] = om1 * mu[0] + om * A.v0;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) rec[k] = (double)(om * G[k]);
-        rec[6] = -(double)(om * om) * (double)gt;
+            for (int k = 0; k < Lat<Q>::P; ++k) {
+                const int i = 2 * k + 1;
+                const T cv = vdot<T>(vel<Q>(i), v[0], v[1], v[2]);
+                lam.p[i][c.n] = om1 * mu[i] + om * (A.v0 + cv);
+                lam.p[i + 1][c.n] = om1 * mu[i + 1] + om * (A.v0 - cv);
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) rec[k] = om * G[k];
+            rec[6] = -(om * om) * (A.gE - smd);
+        }
     }
-    accumulate_record(rec, gpart);
+    accumulate_record<T>(rec, gpart);
 }
 
 template <int Q, typename T>
 __global__ void __launch_bounds__(256) k_adj_init(Geom g, Coef<T> cf, const T* __restrict__ rho0,
-                                                  const T* __restrict__ u0, const T* __restrict__ lam0,
+                                                  const T* __restrict__ u0, const Planes<const T> lam0,
                                                   T* __restrict__ du0, double* __restrict__ gpart) {
-    double rec[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    T rec[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
     Cell c;
-    const bool live = make_cell(g, c);
-    if (live) {
-        const long long N = g.N;
-        const bool solid = g.mask && solid_self(g, c);
+    if (make_cell(g, c)) {
+        const size_t N = g.N;
+        const bool solid = g.link && (__ldg(g.link + c.n) & LINK_SOLID);
         if (solid) {
             if (du0)
                 for (int a = 0; a < Lat<Q>::D; ++a) du0[a * N + c.n] = T(0);
@@ -694,17 +756,17 @@ __global__ void __launch_bounds__(256) k_adj_init(Geom g, Coef<T> cf, const T* _
             const EqCell<T> e = eq_cell<T>(cf, rho - cf.rho0, rho, ux, uy, uz);
             T mu[Q];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) mu[i] = lam0[(long long)i * N + c.n];
-            const AdjAcc<T> A = adj_accumulate<Q, T>(cf, e, mu, nullptr, nullptr);
+            for (int i = 0; i < Q; ++i) mu[i] = lam0.p[i][c.n];
+            const AdjAcc<T> A = adj_accumulate<Q, T>(cf, e, mu);
             T v[3], G[6];
             adj_finish<Q, T>(cf, e, A, v, G);
             if (du0)
                 for (int a = 0; a < Lat<Q>::D; ++a) du0[a * N + c.n] = rho * v[a];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) rec[k] = (double)G[k];
+            for (int k = 0; k < 6; ++k) rec[k] = G[k];
         }
     }
-    accumulate_record(rec, gpart);
+    accumulate_record<T>(rec, gpart);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -715,6 +777,10 @@ struct Launch {
     using ST = typename Store<S>::type;
     using T = typename Store<S>::T;
     using CF = Coef<T>;
+    static Planes<const ST> cpl(const void* p, const Geom& g) { return planes_of(static_cast<const ST*>(p), Q, g.N); }
+    static Planes<ST> mpl(void* p, const Geom& g) { return planes_of(static_cast<ST*>(p), Q, g.N); }
+    static Planes<const T> cfl(const void* p, const Geom& g) { return planes_of(static_cast<const T*>(p), Q, g.N); }
+    static Planes<T> mfl(void* p, const Geom& g) { return planes_of(static_cast<T*>(p), Q, g.N); }
 
     static cudaError_t init(const Geom& g, const void* coef, int layout, const void* rho, const void* u, void* dst,
                             cudaStream_t st) {
@@ -722,8 +788,8 @@ struct Launch {
         const CF& cf = *static_cast<const CF*>(coef);
         auto r = static_cast<const T*>(rho);
         auto uu = static_cast<const T*>(u);
-        auto o = static_cast<ST*>(dst);
-        const bool m = g.mask != nullptr;
+        const auto o = mpl(dst, g);
+        const bool m = g.link != nullptr;
         if (layout == LAYOUT_PULL) {
             if (m)
                 k_init<Q, S, true, LAYOUT_PULL><<<sh.grid, sh.block, 0, st>>>(g, cf, r, uu, o);
@@ -742,9 +808,9 @@ struct Launch {
                                  cudaStream_t st) {
         const Shape sh = shape_for(g);
         const CF& cf = *static_cast<const CF*>(coef);
-        auto a = static_cast<const ST*>(src);
-        auto b = static_cast<ST*>(dst);
-        if (g.mask)
+        const auto a = cpl(src, g);
+        const auto b = mpl(dst, g);
+        if (g.link)
             k_step_pull<Q, S, true><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
         else
             k_step_pull<Q, S, false><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
@@ -755,9 +821,9 @@ struct Launch {
                                cudaStream_t st) {
         const Shape sh = shape_for(g);
         const CF& cf = *static_cast<const CF*>(coef);
-        auto a = static_cast<const ST*>(src);
-        auto b = static_cast<ST*>(dst);
-        if (g.mask) {
+        const auto a = cpl(src, g);
+        const auto b = mpl(dst, g);
+        if (g.link) {
             if (odd)
                 k_step_aa<Q, S, true, 1><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
             else
@@ -774,7 +840,7 @@ struct Launch {
 // Expands to the three layouts times mask / no mask for a kernel template K<Q, S, MASK, LAYOUT>.
 #define LBM_BY_LAYOUT(K, ...)                                                                      \
     do {                                                                                           \
-        const bool m_ = g.mask != nullptr;                                                         \
+        const bool m_ = g.link != nullptr;                                                         \
         if (layout == LAYOUT_PULL) {                                                               \
             if (m_) K<Q, S, true, LAYOUT_PULL><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);         \
             else K<Q, S, false, LAYOUT_PULL><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);           \
@@ -791,7 +857,7 @@ struct Launch {
                                void* Pi, void* f, cudaStream_t st) {
         const Shape sh = shape_for(g);
         const CF& cf = *static_cast<const CF*>(coef);
-        LBM_BY_LAYOUT(k_moments, g, cf, static_cast<const ST*>(src), static_cast<T*>(rho), static_cast<T*>(u),
+        LBM_BY_LAYOUT(k_moments, g, cf, cpl(src, g), static_cast<T*>(rho), static_cast<T*>(u),
                       static_cast<T*>(Pi), static_cast<T*>(f));
         return cudaGetLastError();
     }
@@ -800,7 +866,7 @@ struct Launch {
                               cudaStream_t st) {
         const Shape sh = shape_for(g);
         const CF& cf = *static_cast<const CF*>(coef);
-        LBM_BY_LAYOUT(k_totals, g, cf, static_cast<const ST*>(src), part, flag);
+        LBM_BY_LAYOUT(k_totals, g, cf, cpl(src, g), part, flag);
         return cudaGetLastError();
     }
 
@@ -808,8 +874,7 @@ struct Launch {
                                 void* lam, cudaStream_t st) {
         const Shape sh = shape_for(g);
         const CF& cf = *static_cast<const CF*>(coef);
-        LBM_BY_LAYOUT(k_adj_seed, g, cf, static_cast<const ST*>(src), static_cast<const T*>(grad),
-                      static_cast<T*>(lam));
+        LBM_BY_LAYOUT(k_adj_seed, g, cf, cpl(src, g), static_cast<const T*>(grad), mfl(lam, g));
         return cudaGetLastError();
     }
 
@@ -817,8 +882,7 @@ struct Launch {
                                 void* lam, double* gpart, cudaStream_t st) {
         const Shape sh = shape_for(g);
         const CF& cf = *static_cast<const CF*>(coef);
-        LBM_BY_LAYOUT(k_adj_step, g, cf, static_cast<const ST*>(src), static_cast<const T*>(lam_next),
-                      static_cast<T*>(lam), gpart);
+        LBM_BY_LAYOUT(k_adj_step, g, cf, cpl(src, g), cfl(lam_next, g), mfl(lam, g), gpart);
         return cudaGetLastError();
     }
 #undef LBM_BY_LAYOUT
@@ -828,12 +892,19 @@ struct Launch {
         const Shape sh = shape_for(g);
         const CF& cf = *static_cast<const CF*>(coef);
         k_adj_init<Q, T><<<sh.grid, sh.block, 0, st>>>(g, cf, static_cast<const T*>(rho0), static_cast<const T*>(u0),
-                                                       static_cast<const T*>(lam0), static_cast<T*>(du0), gpart);
+                                                       cfl(lam0, g), static_cast<T*>(du0), gpart);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t link_mask(const Geom& g, const uint8_t* solid, uint32_t* link, cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        k_link_mask<Q><<<sh.grid, sh.block, 0, st>>>(g, solid, link);
         return cudaGetLastError();
     }
 
     static const Ops& ops() {
-        static const Ops o = {&init, &step_pull, &step_aa, &moments, &totals, &adj_seed, &adj_step, &adj_init};
+        static const Ops o = {&init, &step_pull, &step_aa, &moments, &totals, &adj_seed, &adj_step, &adj_init,
+                              &link_mask};
         return o;
     }
 };

@@ -55,6 +55,7 @@ SIGNATURES = {
     "lbm_populations": (_I, [_P, _P]),
     "lbm_totals": (_I, [_P, _P, _P]),
     "lbm_adjoint": (_I, [_P, _P, _I, _I]),
+    "lbm_record_checkpoints": (_I, [_P, _I]),
     "lbm_gradients": (_I, [_P, _P, _P, _P]),
     "lbm_state_bytes": (_I, [_P, ctypes.POINTER(_S)]),
     "lbm_get_state": (_I, [_P, _P, _S]),
@@ -262,6 +263,9 @@ class LBM:
         p = np.zeros(3)
         _check(load().lbm_totals(self.ctx, ctypes.byref(m), p.ctypes.data_as(_P)), self.ctx)
         return m.value, p[: self.d].copy()
+
+    def record_checkpoints(self, checkpoint_every):
+        _check(load().lbm_record_checkpoints(self.ctx, int(checkpoint_every)), self.ctx)
 
     def adjoint(self, loss_grad, n, checkpoint_every=0):
         g = self._field(loss_grad, (self.d, self.N))
