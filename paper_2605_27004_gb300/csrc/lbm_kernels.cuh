@@ -571,13 +571,14 @@ __global__ void __launch_bounds__(256) k_totals(Geom g, Coef<typename Store<S>::
 // ---------------------------------------------------------------------------------------------
 template <typename T>
 struct AdjAcc {
-    T v0, B, P0, Q0, gE;  // gE = sum_i mu_i (feq_i - r_i)
+    T v0, B, P0, Q0, gE;  // gE = sum_i mu_i (feq_i - f_i) when the populations are given
     T Va[3], V[3];
     T P[6], Qm[6];  // xx yy zz xy xz yz
 };
 
 template <int Q, typename T>
-__device__ __forceinline__ AdjAcc<T> adj_accumulate(const Coef<T>& cf, const EqCell<T>& e, const T (&mu)[Q]) {
+__device__ __forceinline__ AdjAcc<T> adj_accumulate(const Coef<T>& cf, const EqCell<T>& e, const T (&mu)[Q],
+                                                    const T* d) {
     AdjAcc<T> A;
     A.v0 = A.B = A.P0 = A.Q0 = A.gE = T(0);
 #pragma unroll
@@ -592,7 +593,7 @@ __device__ __forceinline__ AdjAcc<T> adj_accumulate(const Coef<T>& cf, const EqC
         A.P0 += m;
         A.B += T(3) * m;
         A.v0 += m * (T(1) + T(4.5) * cf.h[0] + T(1.5) * usq);
-        A.gE += mu[0] * rest_eq<Q, T>(cf, e);
+        if (d) A.gE += mu[0] * (rest_eq<Q, T>(cf, e) - d[0]);
     }
 #pragma unroll
     for (int k = 0; k < Lat<Q>::P; ++k) {
@@ -605,7 +606,9 @@ __device__ __forceinline__ AdjAcc<T> adj_accumulate(const Coef<T>& cf, const EqC
         const T sm = w * ms;
         const T dm = w * md;
         const T uc2 = uc * uc;
-        A.gE += E * ms + O * md;
+        // per-direction differences feq_i - f_i: the two operands are close, so each difference is
+        // exact and the small non-equilibrium part keeps its relative precision
+        if (d) A.gE += mu[i] * ((E + O) - d[i]) + mu[i + 1] * ((E - O) - d[i + 1]);
         A.P0 += sm;
         A.Q0 += uc * dm;
         A.B += T(3) * sm + T(2) * c3 * uc * dm;
@@ -709,15 +712,12 @@ __global__ void __launch_bounds__(256) k_adj_step(Geom g, Coef<typename Store<S>
                     p = lam_next.p[i] + off_plus(c, vel<Q>(i));
                 mu[i] = __ldg(p);
             }
-            // f_t: moments and sum_i mu_i (f_i - r_i), without keeping the populations
+            // f_t: moments, and f_i itself for the tau-gradient
             T dk[Q];
             gather<Q, S, MASK, LAYOUT, true>(c, lw, cf, src, dk);
-            T smd = T(0);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) smd += mu[i] * dk[i];
             const Macro<T> m = macro_of<Q, T>(dk, cf.rho0);
             const EqCell<T> e = eq_cell<T>(cf, m.drho, m.rho, m.ux, m.uy, m.uz);
-            const AdjAcc<T> A = adj_accumulate<Q, T>(cf, e, mu);
+            const AdjAcc<T> A = adj_accumulate<Q, T>(cf, e, mu, dk);
             T v[3], G[6];
             adj_finish<Q, T>(cf, e, A, v, G);
             const T om = cf.omega, om1 = T(1) - cf.omega;
@@ -731,7 +731,7 @@ __global__ void __launch_bounds__(256) k_adj_step(Geom g, Coef<typename Store<S>
             }
 #pragma unroll
             for (int k = 0; k < 6; ++k) rec[k] = om * G[k];
-            rec[6] = -(om * om) * (A.gE - smd);
+            rec[6] = -(om * om) * A.gE;
         }
     }
     accumulate_record<T>(rec, gpart);
@@ -757,7 +757,7 @@ __global__ void __launch_bounds__(256) k_adj_init(Geom g, Coef<T> cf, const T* _
             T mu[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) mu[i] = lam0.p[i][c.n];
-            const AdjAcc<T> A = adj_accumulate<Q, T>(cf, e, mu);
+            const AdjAcc<T> A = adj_accumulate<Q, T>(cf, e, mu, nullptr);
             T v[3], G[6];
             adj_finish<Q, T>(cf, e, A, v, G);
             if (du0)
@@ -768,145 +768,5 @@ __global__ void __launch_bounds__(256) k_adj_init(Geom g, Coef<T> cf, const T* _
     }
     accumulate_record<T>(rec, gpart);
 }
-
-// ---------------------------------------------------------------------------------------------
-// Host-side launchers of one (lattice, storage) pair, dispatching over mask and layout.
-// ---------------------------------------------------------------------------------------------
-template <int Q, int S>
-struct Launch {
-    using ST = typename Store<S>::type;
-    using T = typename Store<S>::T;
-    using CF = Coef<T>;
-    static Planes<const ST> cpl(const void* p, const Geom& g) { return planes_of(static_cast<const ST*>(p), Q, g.N); }
-    static Planes<ST> mpl(void* p, const Geom& g) { return planes_of(static_cast<ST*>(p), Q, g.N); }
-    static Planes<const T> cfl(const void* p, const Geom& g) { return planes_of(static_cast<const T*>(p), Q, g.N); }
-    static Planes<T> mfl(void* p, const Geom& g) { return planes_of(static_cast<T*>(p), Q, g.N); }
-
-    static cudaError_t init(const Geom& g, const void* coef, int layout, const void* rho, const void* u, void* dst,
-                            cudaStream_t st) {
-        const Shape sh = shape_for(g);
-        const CF& cf = *static_cast<const CF*>(coef);
-        auto r = static_cast<const T*>(rho);
-        auto uu = static_cast<const T*>(u);
-        const auto o = mpl(dst, g);
-        const bool m = g.link != nullptr;
-        if (layout == LAYOUT_PULL) {
-            if (m)
-                k_init<Q, S, true, LAYOUT_PULL><<<sh.grid, sh.block, 0, st>>>(g, cf, r, uu, o);
-            else
-                k_init<Q, S, false, LAYOUT_PULL><<<sh.grid, sh.block, 0, st>>>(g, cf, r, uu, o);
-        } else {
-            if (m)
-                k_init<Q, S, true, LAYOUT_LOCAL><<<sh.grid, sh.block, 0, st>>>(g, cf, r, uu, o);
-            else
-                k_init<Q, S, false, LAYOUT_LOCAL><<<sh.grid, sh.block, 0, st>>>(g, cf, r, uu, o);
-        }
-        return cudaGetLastError();
-    }
-
-    static cudaError_t step_pull(const Geom& g, const void* coef, const void* src, void* dst, int* flag,
-                                 cudaStream_t st) {
-        const Shape sh = shape_for(g);
-        const CF& cf = *static_cast<const CF*>(coef);
-        const auto a = cpl(src, g);
-        const auto b = mpl(dst, g);
-        if (g.link)
-            k_step_pull<Q, S, true><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
-        else
-            k_step_pull<Q, S, false><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
-        return cudaGetLastError();
-    }
-
-    static cudaError_t step_aa(const Geom& g, const void* coef, int odd, const void* src, void* dst, int* flag,
-                               cudaStream_t st) {
-        const Shape sh = shape_for(g);
-        const CF& cf = *static_cast<const CF*>(coef);
-        const auto a = cpl(src, g);
-        const auto b = mpl(dst, g);
-        if (g.link) {
-            if (odd)
-                k_step_aa<Q, S, true, 1><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
-            else
-                k_step_aa<Q, S, true, 0><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
-        } else {
-            if (odd)
-                k_step_aa<Q, S, false, 1><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
-            else
-                k_step_aa<Q, S, false, 0><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
-        }
-        return cudaGetLastError();
-    }
-
-// Expands to the three layouts times mask / no mask for a kernel template K<Q, S, MASK, LAYOUT>.
-#define LBM_BY_LAYOUT(K, ...)                                                                      \
-    do {                                                                                           \
-        const bool m_ = g.link != nullptr;                                                         \
-        if (layout == LAYOUT_PULL) {                                                               \
-            if (m_) K<Q, S, true, LAYOUT_PULL><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);         \
-            else K<Q, S, false, LAYOUT_PULL><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);           \
-        } else if (layout == LAYOUT_AAODD) {                                                       \
-            if (m_) K<Q, S, true, LAYOUT_AAODD><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);        \
-            else K<Q, S, false, LAYOUT_AAODD><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);          \
-        } else {                                                                                   \
-            if (m_) K<Q, S, true, LAYOUT_LOCAL><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);        \
-            else K<Q, S, false, LAYOUT_LOCAL><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);          \
-        }                                                                                          \
-    } while (0)
-
-    static cudaError_t moments(const Geom& g, const void* coef, int layout, const void* src, void* rho, void* u,
-                               void* Pi, void* f, cudaStream_t st) {
-        const Shape sh = shape_for(g);
-        const CF& cf = *static_cast<const CF*>(coef);
-        LBM_BY_LAYOUT(k_moments, g, cf, cpl(src, g), static_cast<T*>(rho), static_cast<T*>(u),
-                      static_cast<T*>(Pi), static_cast<T*>(f));
-        return cudaGetLastError();
-    }
-
-    static cudaError_t totals(const Geom& g, const void* coef, int layout, const void* src, double* part, int* flag,
-                              cudaStream_t st) {
-        const Shape sh = shape_for(g);
-        const CF& cf = *static_cast<const CF*>(coef);
-        LBM_BY_LAYOUT(k_totals, g, cf, cpl(src, g), part, flag);
-        return cudaGetLastError();
-    }
-
-    static cudaError_t adj_seed(const Geom& g, const void* coef, int layout, const void* src, const void* grad,
-                                void* lam, cudaStream_t st) {
-        const Shape sh = shape_for(g);
-        const CF& cf = *static_cast<const CF*>(coef);
-        LBM_BY_LAYOUT(k_adj_seed, g, cf, cpl(src, g), static_cast<const T*>(grad), mfl(lam, g));
-        return cudaGetLastError();
-    }
-
-    static cudaError_t adj_step(const Geom& g, const void* coef, int layout, const void* src, const void* lam_next,
-                                void* lam, double* gpart, cudaStream_t st) {
-        const Shape sh = shape_for(g);
-        const CF& cf = *static_cast<const CF*>(coef);
-        LBM_BY_LAYOUT(k_adj_step, g, cf, cpl(src, g), cfl(lam_next, g), mfl(lam, g), gpart);
-        return cudaGetLastError();
-    }
-#undef LBM_BY_LAYOUT
-
-    static cudaError_t adj_init(const Geom& g, const void* coef, const void* rho0, const void* u0, const void* lam0,
-                                void* du0, double* gpart, cudaStream_t st) {
-        const Shape sh = shape_for(g);
-        const CF& cf = *static_cast<const CF*>(coef);
-        k_adj_init<Q, T><<<sh.grid, sh.block, 0, st>>>(g, cf, static_cast<const T*>(rho0), static_cast<const T*>(u0),
-                                                       cfl(lam0, g), static_cast<T*>(du0), gpart);
-        return cudaGetLastError();
-    }
-
-    static cudaError_t link_mask(const Geom& g, const uint8_t* solid, uint32_t* link, cudaStream_t st) {
-        const Shape sh = shape_for(g);
-        k_link_mask<Q><<<sh.grid, sh.block, 0, st>>>(g, solid, link);
-        return cudaGetLastError();
-    }
-
-    static const Ops& ops() {
-        static const Ops o = {&init, &step_pull, &step_aa, &moments, &totals, &adj_seed, &adj_step, &adj_init,
-                              &link_mask};
-        return o;
-    }
-};
 
 }  // namespace lbm

@@ -1,0 +1,170 @@
+// Host-side launchers of one (lattice, storage) pair: kernel choice (one or two cells per
+// thread), launch shapes and the dispatch over walls and layouts.
+#pragma once
+#include "lbm_kernels.cuh"
+#include "lbm_pairs.cuh"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------------------------
+template <int Q, int S>
+struct Launch {
+    using ST = typename Store<S>::type;
+    using T = typename Store<S>::T;
+    using CF = Coef<T>;
+    static Planes<const ST> cpl(const void* p, const Geom& g) { return planes_of(static_cast<const ST*>(p), Q, g.N); }
+    static Planes<ST> mpl(void* p, const Geom& g) { return planes_of(static_cast<ST*>(p), Q, g.N); }
+    static Planes<const T> cfl(const void* p, const Geom& g) { return planes_of(static_cast<const T*>(p), Q, g.N); }
+    static Planes<T> mfl(void* p, const Geom& g) { return planes_of(static_cast<T*>(p), Q, g.N); }
+
+    static cudaError_t init(const Geom& g, const void* coef, int layout, const void* rho, const void* u, void* dst,
+                            cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        auto r = static_cast<const T*>(rho);
+        auto uu = static_cast<const T*>(u);
+        const auto o = mpl(dst, g);
+        const bool m = g.link != nullptr;
+        if (layout == LAYOUT_PULL) {
+            if (m)
+                k_init<Q, S, true, LAYOUT_PULL><<<sh.grid, sh.block, 0, st>>>(g, cf, r, uu, o);
+            else
+                k_init<Q, S, false, LAYOUT_PULL><<<sh.grid, sh.block, 0, st>>>(g, cf, r, uu, o);
+        } else {
+            if (m)
+                k_init<Q, S, true, LAYOUT_LOCAL><<<sh.grid, sh.block, 0, st>>>(g, cf, r, uu, o);
+            else
+                k_init<Q, S, false, LAYOUT_LOCAL><<<sh.grid, sh.block, 0, st>>>(g, cf, r, uu, o);
+        }
+        return cudaGetLastError();
+    }
+
+    // the two-cells-per-thread kernels serve the FP32 arithmetic forms on grids with even nx
+    static bool pairs(const Geom& g) { return S != 1 && (g.nx % 2) == 0; }
+
+    static cudaError_t step_pull(const Geom& g, const void* coef, const void* src, void* dst, int* flag,
+                                 cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        const auto a = cpl(src, g);
+        const auto b = mpl(dst, g);
+        if constexpr (S != 1) {
+            if (pairs(g)) {
+                const Shape sp = shape_pairs(g);
+                if (g.link)
+                    k_step_pull2<Q, S, true><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
+                else
+                    k_step_pull2<Q, S, false><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
+                return cudaGetLastError();
+            }
+        }
+        if (g.link)
+            k_step_pull<Q, S, true><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
+        else
+            k_step_pull<Q, S, false><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t step_aa(const Geom& g, const void* coef, int odd, const void* src, void* dst, int* flag,
+                               cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        const auto a = cpl(src, g);
+        const auto b = mpl(dst, g);
+        if constexpr (S != 1) {
+            if (pairs(g) && !odd) {
+                const Shape sp = shape_pairs(g);
+                if (g.link)
+                    k_step_aa_even2<Q, S, true><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
+                else
+                    k_step_aa_even2<Q, S, false><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
+                return cudaGetLastError();
+            }
+        }
+        if (g.link) {
+            if (odd)
+                k_step_aa<Q, S, true, 1><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
+            else
+                k_step_aa<Q, S, true, 0><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
+        } else {
+            if (odd)
+                k_step_aa<Q, S, false, 1><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
+            else
+                k_step_aa<Q, S, false, 0><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
+        }
+        return cudaGetLastError();
+    }
+
+// Expands to the three layouts times mask / no mask for a kernel template K<Q, S, MASK, LAYOUT>.
+#define LBM_BY_LAYOUT(K, ...)                                                                      \
+    do {                                                                                           \
+        const bool m_ = g.link != nullptr;                                                         \
+        if (layout == LAYOUT_PULL) {                                                               \
+            if (m_) K<Q, S, true, LAYOUT_PULL><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);         \
+            else K<Q, S, false, LAYOUT_PULL><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);           \
+        } else if (layout == LAYOUT_AAODD) {                                                       \
+            if (m_) K<Q, S, true, LAYOUT_AAODD><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);        \
+            else K<Q, S, false, LAYOUT_AAODD><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);          \
+        } else {                                                                                   \
+            if (m_) K<Q, S, true, LAYOUT_LOCAL><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);        \
+            else K<Q, S, false, LAYOUT_LOCAL><<<sh.grid, sh.block, 0, st>>>(__VA_ARGS__);          \
+        }                                                                                          \
+    } while (0)
+
+    static cudaError_t moments(const Geom& g, const void* coef, int layout, const void* src, void* rho, void* u,
+                               void* Pi, void* f, cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        LBM_BY_LAYOUT(k_moments, g, cf, cpl(src, g), static_cast<T*>(rho), static_cast<T*>(u),
+                      static_cast<T*>(Pi), static_cast<T*>(f));
+        return cudaGetLastError();
+    }
+
+    static cudaError_t totals(const Geom& g, const void* coef, int layout, const void* src, double* part, int* flag,
+                              cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        LBM_BY_LAYOUT(k_totals, g, cf, cpl(src, g), part, flag);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t adj_seed(const Geom& g, const void* coef, int layout, const void* src, const void* grad,
+                                void* lam, cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        LBM_BY_LAYOUT(k_adj_seed, g, cf, cpl(src, g), static_cast<const T*>(grad), mfl(lam, g));
+        return cudaGetLastError();
+    }
+
+    static cudaError_t adj_step(const Geom& g, const void* coef, int layout, const void* src, const void* lam_next,
+                                void* lam, double* gpart, cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        LBM_BY_LAYOUT(k_adj_step, g, cf, cpl(src, g), cfl(lam_next, g), mfl(lam, g), gpart);
+        return cudaGetLastError();
+    }
+#undef LBM_BY_LAYOUT
+
+    static cudaError_t adj_init(const Geom& g, const void* coef, const void* rho0, const void* u0, const void* lam0,
+                                void* du0, double* gpart, cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        k_adj_init<Q, T><<<sh.grid, sh.block, 0, st>>>(g, cf, static_cast<const T*>(rho0), static_cast<const T*>(u0),
+                                                       cfl(lam0, g), static_cast<T*>(du0), gpart);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t link_mask(const Geom& g, const uint8_t* solid, uint32_t* link, cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        k_link_mask<Q><<<sh.grid, sh.block, 0, st>>>(g, solid, link);
+        return cudaGetLastError();
+    }
+
+    static const Ops& ops() {
+        static const Ops o = {&init, &step_pull, &step_aa, &moments, &totals, &adj_seed, &adj_step, &adj_init,
+                              &link_mask};
+        return o;
+    }
+};
+
+}  // namespace lbm

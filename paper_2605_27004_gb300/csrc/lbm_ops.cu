@@ -1,6 +1,6 @@
 // Kernel instantiations of one (lattice, storage) pair. The build compiles this file once per
 // pair with -DLBM_Q=<9|19|27> -DLBM_S=<0..3>, so the twelve objects build in parallel.
-#include "lbm_kernels.cuh"
+#include "lbm_launch.cuh"
 
 #if !defined(LBM_Q) || !defined(LBM_S)
 #error "compile with -DLBM_Q=<9|19|27> -DLBM_S=<0|1|2|3>"

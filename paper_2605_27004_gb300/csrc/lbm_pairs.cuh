@@ -1,0 +1,324 @@
+// Two-cells-per-thread forward kernels for the FP32 and FP16 storage forms (sm_100+ packed FP32).
+//
+// A thread owns the x-adjacent cells (x0, x0 + 1), x0 even, of one row; a warp owns 64
+// consecutive cells of one row (rows start at lane 0 because blocks are a multiple of 32 threads
+// wide). Every population plane is read and written as aligned 2-element vectors (half2 or
+// float2), which halves the load/store and address instructions per cell. Along x the pull
+// gather needs f(x0 - c_x) and f(x0 + 1 - c_x): for c_x = +1 the element x0 - 1 is the upper
+// half of the previous lane's vector and for c_x = -1 the element x0 + 2 is the lower half of the
+// next lane's vector, so it arrives by one warp shuffle; a lane whose neighbour lane holds no
+// vector (row start or end, or a neighbour pair that is entirely solid or outside the grid)
+// loads that element itself, with periodic wrap. The collision runs on (cell A, cell B) pairs
+// with the packed FP32 instructions (FFMA2 / FADD2 / FMUL2), the same operation order as the
+// one-cell kernels.
+#pragma once
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------------------------------------
+// Packed FP32 pair arithmetic
+// ---------------------------------------------------------------------------------------------
+struct F2 {
+    float2 v;
+};
+__device__ __forceinline__ F2 f2(float a) { return {make_float2(a, a)}; }
+__device__ __forceinline__ F2 f2(float a, float b) { return {make_float2(a, b)}; }
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return {__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return {__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)}; }
+__device__ __forceinline__ F2 operator-(F2 a) { return {make_float2(-a.v.x, -a.v.y)}; }
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ F2& operator+=(F2& a, F2 b) {
+    a = a + b;
+    return a;
+}
+__device__ __forceinline__ F2& operator-=(F2& a, F2 b) {
+    a = a - b;
+    return a;
+}
+
+__device__ __forceinline__ void add_c2(Vec3 v, F2 val, F2& x, F2& y, F2& z) {
+    if (v.x == 1) x += val;
+    if (v.x == -1) x -= val;
+    if (v.y == 1) y += val;
+    if (v.y == -1) y -= val;
+    if (v.z == 1) z += val;
+    if (v.z == -1) z -= val;
+}
+__device__ __forceinline__ F2 vdot2(Vec3 v, F2 ax, F2 ay, F2 az) {
+    F2 r = f2(0.f);
+    bool first = true;
+    auto acc = [&](int s, F2 a) {
+        if (s == 0) return;
+        if (first) {
+            r = s > 0 ? a : -a;
+            first = false;
+        } else if (s > 0) {
+            r += a;
+        } else {
+            r -= a;
+        }
+    };
+    acc(v.x, ax);
+    acc(v.y, ay);
+    acc(v.z, az);
+    return r;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Storage vectors: two consecutive elements of one plane
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ F2 ld2(const float* p) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return {v};
+}
+__device__ __forceinline__ F2 ld2(const __half* p) {
+    const unsigned int w = __ldg(reinterpret_cast<const unsigned int*>(p));
+    return {__half22float2(*reinterpret_cast<const __half2*>(&w))};
+}
+__device__ __forceinline__ F2 ld2_rw(const float* p) { return {*reinterpret_cast<const float2*>(p)}; }
+__device__ __forceinline__ F2 ld2_rw(const __half* p) {
+    const unsigned int w = *reinterpret_cast<const unsigned int*>(p);
+    return {__half22float2(*reinterpret_cast<const __half2*>(&w))};
+}
+__device__ __forceinline__ void st2(float* p, F2 v) { *reinterpret_cast<float2*>(p) = v.v; }
+__device__ __forceinline__ void st2(__half* p, F2 v) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v); }
+
+template <int S>
+__device__ __forceinline__ F2 to_shifted2(F2 raw, float r) {
+    return Store<S>::shifted ? raw : raw - f2(r);
+}
+template <int S>
+__device__ __forceinline__ F2 from_shifted2(F2 d, float r) {
+    return Store<S>::shifted ? d : d + f2(r);
+}
+
+// Pair cell: thread (lane) owns x0 and x0 + 1 of row (y, z).
+struct PCell {
+    int x0, y, z, lane;
+    bool in_grid;    // the pair lies inside the grid
+    bool active;     // in the grid and not entirely solid
+    bool prev_ok;    // the previous lane holds an active pair of the same row
+    bool next_ok;    // the next lane holds an active pair of the same row
+    uint32_t n;      // index of cell x0
+    uint32_t X[3];   // wrapped x0 + 1, x0, x0 - 1 (only X[1] is used for vector access)
+    uint32_t R[3][3];
+};
+
+__device__ __forceinline__ void make_pcell(const Geom& g, PCell& c) {
+    const int px = blockIdx.x * blockDim.x + threadIdx.x;
+    c.x0 = 2 * px;
+    c.y = blockIdx.y * blockDim.y + threadIdx.y;
+    c.z = blockIdx.z;
+    c.lane = (threadIdx.x + threadIdx.y * blockDim.x) & 31;
+    c.in_grid = c.x0 < g.nx && c.y < g.ny;
+    // clamp out-of-grid lanes to a valid pair so that any address they form is in bounds
+    const int x0 = c.in_grid ? c.x0 : 0;
+    const int y = c.y < g.ny ? c.y : 0;
+    const uint32_t yy[3] = {(uint32_t)(y + 1 == g.ny ? 0 : y + 1), (uint32_t)y, (uint32_t)(y == 0 ? g.ny - 1 : y - 1)};
+    const uint32_t zz[3] = {(uint32_t)(c.z + 1 == g.nz ? 0 : c.z + 1), (uint32_t)c.z,
+                            (uint32_t)(c.z == 0 ? g.nz - 1 : c.z - 1)};
+    const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) c.R[a][b] = nx * (yy[a] + ny * zz[b]);
+    c.X[1] = (uint32_t)x0;
+    c.n = (uint32_t)x0 + c.R[1][1];
+    c.x0 = x0;
+}
+
+__device__ __forceinline__ void pcell_neighbours(PCell& c) {
+    const unsigned am = __ballot_sync(FULL, c.active);
+    c.prev_ok = c.lane > 0 && ((am >> (c.lane - 1)) & 1u) && c.x0 > 0;
+    c.next_ok = c.lane < 31 && ((am >> (c.lane + 1)) & 1u);
+}
+
+// f(x0 - cx) and f(x0 + 1 - cx) of the row at element offset `row` of plane p (pull shift).
+template <int S, bool RO>
+__device__ __forceinline__ F2 gather_pair(const typename Store<S>::type* p, uint32_t row, const PCell& c, int cx,
+                                          int nx, float r) {
+    F2 v = f2(0.f);
+    if (c.active) v = RO ? ld2(p + row + c.x0) : ld2_rw(p + row + c.x0);
+    if (cx == 1) {
+        const float prev = __shfl_up_sync(FULL, v.v.y, 1);
+        float a = prev;
+        if (c.active && !c.prev_ok) {
+            const int xm = c.x0 == 0 ? nx - 1 : c.x0 - 1;
+            a = RO ? ld_ro(p + row + xm) : ld_rw(p + row + xm);
+        }
+        v = f2(a, v.v.x);
+    } else if (cx == -1) {
+        const float next = __shfl_down_sync(FULL, v.v.x, 1);
+        float b = next;
+        if (c.active && !c.next_ok) {
+            const int xp = c.x0 + 2 == nx ? 0 : c.x0 + 2;
+            b = RO ? ld_ro(p + row + xp) : ld_rw(p + row + xp);
+        }
+        v = f2(v.v.y, b);
+    }
+    return to_shifted2<S>(v, r);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pair collision (same arithmetic as bgk<Q, float, FIX>, two cells per instruction)
+// ---------------------------------------------------------------------------------------------
+struct Macro2 {
+    F2 drho, rho, jx, jy, jz, ux, uy, uz;
+};
+
+template <int Q, bool FIX>
+__device__ __forceinline__ Macro2 bgk2(const Coef<float>& cf, F2 (&d)[Q]) {
+    Macro2 m;
+    F2 s = d[0], jx = f2(0.f), jy = f2(0.f), jz = f2(0.f);
+#pragma unroll
+    for (int k = 0; k < Lat<Q>::P; ++k) {
+        const F2 a = d[2 * k + 1], b = d[2 * k + 2];
+        s += a + b;
+        add_c2(vel<Q>(2 * k + 1), a - b, jx, jy, jz);
+    }
+    m.drho = s;
+    m.rho = f2(cf.rho0) + s;
+    m.jx = jx;
+    m.jy = jy;
+    m.jz = jz;
+    const F2 inv = f2(1.f / m.rho.v.x, 1.f / m.rho.v.y);
+    m.ux = jx * inv;
+    m.uy = jy * inv;
+    m.uz = Lat<Q>::D == 3 ? jz * inv : f2(0.f);
+    const F2 usq = fma2(m.ux, m.ux, fma2(m.uy, m.uy, m.uz * m.uz));
+    const F2 kx = fma2(f2(cf.K[0]), m.ux, fma2(f2(cf.K[3]), m.uy, f2(cf.K[4]) * m.uz));
+    const F2 ky = fma2(f2(cf.K[3]), m.ux, fma2(f2(cf.K[1]), m.uy, f2(cf.K[5]) * m.uz));
+    const F2 kz = fma2(f2(cf.K[4]), m.ux, fma2(f2(cf.K[5]), m.uy, f2(cf.K[2]) * m.uz));
+    const F2 r45 = f2(4.5f) * m.rho;
+    const F2 usq3 = usq * f2(1.0f / 3.0f);
+    const F2 om = f2(cf.omega), om1 = f2(1.f - cf.omega);
+    {
+        const F2 feq = fma2(m.drho, f2(cf.A[0]), -(f2((float)weight<Q>(0)) * r45 * usq3));
+        d[0] = fma2(om1, d[0], om * feq);
+    }
+#pragma unroll
+    for (int k = 0; k < Lat<Q>::P; ++k) {
+        const int i = 2 * k + 1;
+        const Vec3 v = vel<Q>(i);
+        const F2 w = f2((float)weight<Q>(i));
+        const F2 uc = vdot2(v, m.ux, m.uy, m.uz);
+        const F2 qk = vdot2(v, kx, ky, kz);
+        const F2 E = fma2(m.drho, f2(cf.A[i]), w * r45 * fma2(uc, uc, -usq3));
+        const F2 cub = fma2(uc, fma2(uc, uc, -usq), -(f2(2.f) * qk));
+        const F2 O = m.rho * fma2(uc, f2(cf.B[i]), w * f2(cf.c3) * cub);
+        d[i] = fma2(om1, d[i], om * (E + O));
+        d[i + 1] = fma2(om1, d[i + 1], om * (E - O));
+    }
+    if (FIX) {
+        F2 ex = -m.jx, ey = -m.jy, ez = -m.jz;
+#pragma unroll
+        for (int k = 0; k < Lat<Q>::P; ++k) add_c2(vel<Q>(2 * k + 1), d[2 * k + 1] - d[2 * k + 2], ex, ey, ez);
+#pragma unroll
+        for (int k = 0; k < Lat<Q>::P; ++k) {
+            const Vec3 v = vel<Q>(2 * k + 1);
+            const F2 corr = f2((float)(3.0 * weight<Q>(2 * k + 1))) * vdot2(v, ex, ey, ez);
+            d[2 * k + 1] -= corr;
+            d[2 * k + 2] += corr;
+        }
+    }
+    return m;
+}
+
+__device__ __forceinline__ bool bad1(float rho, float ux, float uy, float uz) {
+    return !(rho > 0.f) || !isfinite(ux + uy + uz);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pull step, two cells per thread.
+// ---------------------------------------------------------------------------------------------
+template <int Q, int S, bool MASK>
+__global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_pull2(Geom g, Coef<float> cf,
+                                                    const Planes<const typename Store<S>::type> src,
+                                                    const Planes<typename Store<S>::type> dst, int* __restrict__ flag) {
+    PCell c;
+    make_pcell(g, c);
+    uint2 lw = make_uint2(0u, 0u);
+    if (MASK && c.in_grid) lw = __ldg(reinterpret_cast<const uint2*>(g.link + c.n));
+    const bool fa = !(lw.x & LINK_SOLID), fb = !(lw.y & LINK_SOLID);
+    c.active = c.in_grid && (fa || fb);
+    pcell_neighbours(c);
+    F2 d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const Vec3 v = vel<Q>(i);
+        d[i] = gather_pair<S, true>(src.p[i], c.R[v.y + 1][v.z + 1], c, v.x, g.nx, cf.r[i]);
+        if (MASK && i > 0) {
+            const bool wa = link_bit(lw.x, i), wb = link_bit(lw.y, i);
+            if (c.active && (wa || wb)) {  // half-way bounce-back from the own cell's opposite slot
+                const F2 own = to_shifted2<S>(ld2(src.p[opp(i)] + c.n), cf.r[i]);
+                d[i] = f2(wa ? own.v.x : d[i].v.x, wb ? own.v.y : d[i].v.y);
+            }
+        }
+    }
+    if (!c.active) return;
+    const Macro2 m = bgk2<Q, Store<S>::fix_momentum>(cf, d);
+    if ((fa && bad1(m.rho.v.x, m.ux.v.x, m.uy.v.x, m.uz.v.x)) || (fb && bad1(m.rho.v.y, m.ux.v.y, m.uy.v.y, m.uz.v.y)))
+        *flag = 1;
+    if (!MASK || (fa && fb)) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) st2(dst.p[i] + c.n, from_shifted2<S>(d[i], cf.r[i]));
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const F2 o = from_shifted2<S>(d[i], cf.r[i]);
+            if (fa) st_raw(dst.p[i] + c.n, o.v.x);
+            if (fb) st_raw(dst.p[i] + c.n + 1, o.v.y);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// AA even step (state LOCAL -> AAODD), two cells per thread: purely local.
+// ---------------------------------------------------------------------------------------------
+template <int Q, int S, bool MASK>
+__global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_aa_even2(Geom g, Coef<float> cf,
+                                                       const Planes<const typename Store<S>::type> src,
+                                                       const Planes<typename Store<S>::type> dst,
+                                                       int* __restrict__ flag) {
+    PCell c;
+    make_pcell(g, c);
+    if (!c.in_grid) return;
+    uint2 lw = make_uint2(0u, 0u);
+    if (MASK) lw = __ldg(reinterpret_cast<const uint2*>(g.link + c.n));
+    const bool fa = !(lw.x & LINK_SOLID), fb = !(lw.y & LINK_SOLID);
+    if (!fa && !fb) return;
+    F2 d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = to_shifted2<S>(ld2_rw(src.p[i] + c.n), cf.r[i]);
+    const Macro2 m = bgk2<Q, Store<S>::fix_momentum>(cf, d);
+    if ((fa && bad1(m.rho.v.x, m.ux.v.x, m.uy.v.x, m.uz.v.x)) || (fb && bad1(m.rho.v.y, m.ux.v.y, m.uy.v.y, m.uz.v.y)))
+        *flag = 1;
+    if (!MASK || (fa && fb)) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) st2(dst.p[opp(i)] + c.n, from_shifted2<S>(d[i], cf.r[i]));
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const F2 o = from_shifted2<S>(d[i], cf.r[i]);
+            if (fa) st_raw(dst.p[opp(i)] + c.n, o.v.x);
+            if (fb) st_raw(dst.p[opp(i)] + c.n + 1, o.v.y);
+        }
+    }
+}
+
+inline Shape shape_pairs(const Geom& g) {
+    Shape s;
+    const int np = g.nx / 2;
+    const int bx = np >= 256 ? 256 : ((np + 31) / 32) * 32;
+    const int by = 256 / bx;
+    s.block = dim3(bx, by, 1);
+    s.grid = dim3((np + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
+    s.nblocks = (long long)s.grid.x * s.grid.y * s.grid.z;
+    return s;
+}
+
+}  // namespace lbm
