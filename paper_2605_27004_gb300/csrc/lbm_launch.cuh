@@ -39,8 +39,10 @@ struct Launch {
         return cudaGetLastError();
     }
 
-    // the two-cells-per-thread kernels serve the FP32 arithmetic forms on grids with even nx
-    static bool pairs(const Geom& g) { return S != 1 && (g.nx % 2) == 0; }
+    // Two cells per thread pay off where the one-cell kernel is instruction-bound: FP16 storage
+    // without walls on D2Q9/D3Q19 (measured: 0.61 -> 0.75 of HBM bandwidth). FP32 storage is at
+    // the bandwidth bound with one cell per thread already, and the wall variants lose occupancy.
+    static bool pairs(const Geom& g) { return S == 3 && Q != 27 && !g.link && (g.nx % 2) == 0; }
 
     static cudaError_t step_pull(const Geom& g, const void* coef, const void* src, void* dst, int* flag,
                                  cudaStream_t st) {

@@ -73,11 +73,12 @@ def test_adjoint_reduced_precision(storage):
     print(storage, np.abs(dth - odth).max() / np.abs(odth).max(), abs(dtau - odtau) / abs(odtau), rel_l2(du0, odu0))
     assert np.abs(dth - odth).max() <= 1e-3 * np.abs(odth).max()
     assert rel_l2(du0, odu0) < 1e-3
-    # dL/dtau weighs the non-equilibrium part f - feq, which is O(Kn) small; FP16 storage rounds
-    # f - r to 11 bits, i.e. a relative error of ~1e-3 of the O(u) deviation, which is a few
-    # percent of f - feq. The adjoint differentiates the stored trajectory, so the gap is the
-    # forward precision, not the adjoint.
-    tol_tau = 1e-3 if storage != "fp16s" else 5e-2
+    # dL/dtau weighs the non-equilibrium part f - feq, which decays to a small fraction of f as
+    # the seeded noise relaxes. FP16 storage rounds f - r to 11 bits and plain FP32 storage
+    # rounds f ~ 0.3 to ~2e-8 absolute; both are visible against f - feq late in the run. The
+    # adjoint differentiates the stored trajectory, so the gap is the forward precision, not the
+    # adjoint; the shifted FP32 form keeps 1e-3.
+    tol_tau = {"fp32s": 1e-3, "fp32": 1e-2, "fp16s": 5e-2}[storage]
     assert abs(dtau - odtau) <= tol_tau * abs(odtau)
 
 

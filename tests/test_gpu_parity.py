@@ -211,7 +211,8 @@ def test_fp32_and_fp16_kernels_match_oracle(q, dims, storage, scheme, mask):
     g = gpu_run(q, dims, 0.7, Th, rho0, u0, 40, solid=solid, storage=storage, scheme=scheme)
     o = oracle_run(q, dims, 0.7, Th, rho0, u0, 40, solid=solid)
     fl = slice(None) if solid is None else (solid == 0)
-    tol = 1e-3 if storage == "fp16s" else 2e-6
+    # plain FP32 stores f ~ 0.3 with an absolute rounding of ~2e-8 per step against u ~ 1e-3
+    tol = {"fp16s": 1e-3, "fp32": 2e-5, "fp32s": 2e-6}[storage]
     assert rel_l2(g["u"][:, fl], o["u"][:, fl]) < tol
     perm = perm_lib_to_oracle(q)
     f_or = o["f"][:, perm].T
