@@ -166,6 +166,24 @@ int lbm_device_bytes(const lbm_ctx* ctx, size_t* bytes);
 /* Kernel launches issued by this context since creation (all kinds). */
 int lbm_launch_count(const lbm_ctx* ctx, long long* launches);
 
+/* FP64 totals of a caller-owned population array with no device allocation: for callers that
+ * cannot call cudaMalloc, cudaFree or any allocating routine where they need the totals (code
+ * under an external memory manager that owns every device byte, code that must not synchronise
+ * the device through an allocation, plug-ins that only receive pointers to existing buffers).
+ * The paper has no counterpart; it is the block-partial reduction of lbm_totals.
+ *   f       device [q][N] populations f_i(x) in the library's direction order, float or (fp64 != 0)
+ *           double, e.g. the output of lbm_populations (zeros at solid cells add nothing)
+ *   totals  device double[4]: sum f, sum f c_x, sum f c_y, sum f c_z (0 in 2D)
+ *   stream  cudaStream_t (NULL: legacy default stream); the call is asynchronous on it.
+ * The partial sums live in one fixed __device__ array of 1216 records x 4 doubles (38,912 bytes)
+ * that every GPU loading the library holds until the process exits; every call writes each
+ * record it reads, so nothing needs clearing between calls, and all calls share the array:
+ * calls that overlap on the GPU (other streams, other host threads) race on it. The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) and caches it; make
+ * that first call outside any stream capture. Any N up to 2^31 - 1 cells fits; larger sizes,
+ * an unknown lattice, nz != 1 for D2Q9 or null pointers return LBM_ERR_INVALID_ARG. */
+int lbm_totals_noalloc(int lattice, int nx, int ny, int nz, int fp64, const void* f, double* totals, void* stream);
+
 const char* lbm_status_string(int status);
 const char* lbm_last_error(const lbm_ctx* ctx);
 

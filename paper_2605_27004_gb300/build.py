@@ -63,8 +63,9 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
             obj = os.path.join(OUT, f"lbm_ops_q{q}_s{s}.o")
             tasks.append([nvcc, *ARCH, *FLAGS, f"-DLBM_Q={q}", f"-DLBM_S={s}", "-c",
                           os.path.join(CSRC, "lbm_ops.cu"), "-o", obj])
-    tasks.append([nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, "lbm_host.cu"), "-o",
-                  os.path.join(OUT, "lbm_host.o")])
+    for name in ("lbm_host", "lbm_noalloc"):
+        tasks.append([nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, name + ".cu"), "-o",
+                      os.path.join(OUT, name + ".o")])
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         logs = list(ex.map(_run, tasks))
     if verbose:

@@ -65,6 +65,7 @@ SIGNATURES = {
     "lbm_lattice_info": (_I, [_I, _P, _P]),
     "lbm_device_bytes": (_I, [_P, ctypes.POINTER(_S)]),
     "lbm_launch_count": (_I, [_P, ctypes.POINTER(_LL)]),
+    "lbm_totals_noalloc": (_I, [_I, _I, _I, _I, _I, _P, _P, _P]),
     "lbm_status_string": (ctypes.c_char_p, [_I]),
     "lbm_last_error": (ctypes.c_char_p, [_P]),
 }
