@@ -35,12 +35,15 @@ ELEM = {"fp32": 4, "fp32s": 4, "fp16s": 2, "fp64": 8}
 
 # DRAM bytes per launch from an ncu capture (profiles/), keyed by variant; used only while the
 # kernel sources hash to the recorded value (otherwise the bench reports traffic = null).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/k_step_pull_d3q19_fp32_256.md: mean of 3 launches, 256^3, read 1.2751e9 + write 1.2208e9
+    "d3q19_fp32_pull": {"traffic_bytes": 2.4959e9, "kernel_sha": "f4fa447af7b68ba6"},
+}
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("lbm_kernels.cuh", "lbm_lattice.cuh", "lbm_internal.h"):
+    for f in ("lbm_kernels.cuh", "lbm_lattice.cuh", "lbm_internal.h", "lbm_launch.cuh", "lbm_pairs.cuh"):
         with open(os.path.join(ROOT, "paper_2605_27004_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
