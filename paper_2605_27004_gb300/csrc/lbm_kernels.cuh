@@ -513,17 +513,19 @@ __global__ void __launch_bounds__(256) k_moments(Geom g, Coef<typename Store<S>:
 }
 
 // ---------------------------------------------------------------------------------------------
-// Block reductions. Thread 0 of the block ends with the sums.
-// FP64 throughout for totals; for gradient records the 32 lanes of a warp are summed in the
-// arithmetic type first, then the warps and all later accumulation are FP64.
+// Block reductions: FP64 throughout for totals; for gradient records the 32 lanes of a warp are
+// summed in the arithmetic type first, then the warps and all later accumulation are FP64.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ long long block_linear() {
     return (long long)blockIdx.x + (long long)gridDim.x * ((long long)blockIdx.y + (long long)gridDim.y * blockIdx.z);
 }
 
+// Block sum of W values per thread. The 32 lanes of a warp are added in the value type T; then
+// thread k < W adds component k of the (at most 8) warp sums in FP64, in parallel. Returns the
+// block sum of component tid for threads tid < W (0 for the others).
 template <int W, typename T>
-__device__ __forceinline__ void block_sum_to_double(T (&v)[W], double (&out)[W]) {
-    __shared__ double sh[8][W];
+__device__ __forceinline__ double block_sum_lane(T (&v)[W]) {
+    __shared__ T sh[8][W];
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
@@ -532,20 +534,13 @@ __device__ __forceinline__ void block_sum_to_double(T (&v)[W], double (&out)[W])
         T s = v[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        v[k] = s;
+        if (lane == 0) sh[warp][k] = s;
     }
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < W; ++k) sh[warp][k] = (double)v[k];
     __syncthreads();
-    if (tid == 0) {
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-            double s = 0.0;
-            for (int w = 0; w < nwarps; ++w) s += sh[w][k];
-            out[k] = s;
-        }
-    }
+    double s = 0.0;
+    if (tid < W)
+        for (int w = 0; w < nwarps; ++w) s += (double)sh[w][tid];
+    return s;
 }
 
 // Totals over fluid cells: partial[block][0] = sum rho, [1..3] = sum j, in FP64.
@@ -569,13 +564,9 @@ __global__ void __launch_bounds__(256) k_totals(Geom g, Coef<typename Store<S>::
             v[3] = (double)m.jz;
         }
     }
-    double out[4];
-    block_sum_to_double<4, double>(v, out);
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        const long long b = block_linear();
-#pragma unroll
-        for (int k = 0; k < 4; ++k) partials[b * 4 + k] = out[k];
-    }
+    const double s = block_sum_lane<4, double>(v);
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    if (tid < 4) partials[block_linear() * 4 + tid] = s;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -681,15 +672,12 @@ __device__ __forceinline__ void adj_finish(const Coef<T>& cf, const EqCell<T>& e
 }
 
 // Gradient record per block: [0..5] Theta (xx yy zz xy xz yz), [6] tau, [7] unused.
+// Each block accumulates into its own record, in launch order, so the result is deterministic.
 template <typename T>
 __device__ __forceinline__ void accumulate_record(T (&v)[8], double* gpart) {
-    double out[8];
-    block_sum_to_double<8, T>(v, out);
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        const long long b = block_linear();
-#pragma unroll
-        for (int k = 0; k < 8; ++k) gpart[b * 8 + k] += out[k];
-    }
+    const double s = block_sum_lane<8, T>(v);
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    if (tid < 8) gpart[block_linear() * 8 + tid] += s;
 }
 
 template <int Q, int S, bool MASK, int LAYOUT>
