@@ -123,6 +123,7 @@ struct lbm_ctx {
     void* du0 = nullptr;
     double* gpart = nullptr;
     bool grads_ready = false;
+    int last_adj_K2 = 0;  // sub-segment length of the last adjoint (== K when flat)
     double grad_theta[6] = {0};
     double grad_tau = 0.0;
 
@@ -346,15 +347,23 @@ void* ckpt_slot(lbm_ctx* c, size_t k, bool* host) {
         c->rec_ptr.resize(k + 1, nullptr);
         c->rec_host.resize(k + 1, false);
     }
-    size_t limit = c->opt.adjoint_mem_limit;
-    size_t fr = 0, tot = 0;
-    if (limit == 0 && cudaMemGetInfo(&fr, &tot) == cudaSuccess) limit = fr > ((size_t)4 << 30) ? fr - ((size_t)4 << 30) : 0;
+    // Device memory while the checkpoints stay within adjoint_mem_limit and leave room for the
+    // adjoint's own working set (two lambda arrays, du0, and the smallest two-level segment
+    // plan, 2 sqrt(K) states); pinned host memory beyond.
     size_t used = 0;
     for (size_t j = 0; j < c->rec_ptr.size(); ++j)
         if (c->rec_ptr[j] && !c->rec_host[j]) used += SB;
+    size_t fr = 0, tot = 0;
+    bool dev_ok = cudaMemGetInfo(&fr, &tot) == cudaSuccess;
+    if (!dev_ok) (void)cudaGetLastError();
+    const size_t LB = (size_t)c->q * c->N * c->felem;
+    const size_t reserve = (c->lam[0] ? 0 : 2 * LB + (size_t)c->d * c->N * c->felem) +
+                           (size_t)(2 * (int)std::ceil(std::sqrt((double)c->rec_K)) + 1) * SB + ((size_t)2 << 30);
+    dev_ok = dev_ok && fr >= reserve + SB;
+    if (c->opt.adjoint_mem_limit) dev_ok = dev_ok && used + SB <= c->opt.adjoint_mem_limit;
     void* p = nullptr;
     bool h = false;
-    if (used + SB <= limit) p = dev_alloc(c, SB);
+    if (dev_ok) p = dev_alloc(c, SB);
     if (!p) {
         if (cudaMallocHost(&p, SB) != cudaSuccess) {
             (void)cudaGetLastError();
@@ -736,14 +745,35 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
     LBM_CUDA(c, cudaMemsetAsync(c->gpart, 0, GB, c->stream));
     c->grads_ready = false;
 
-    const int C = (n + K - 1) / K;  // checkpoints at t = 0, K, ..., (C-1)K
-    // Recorded checkpoints of the forward run are used when they cover [0, n) with this K.
+    const int C = (n + K - 1) / K;  // top-level checkpoints at t = 0, K, ..., (C-1)K
     const bool recorded = c->rec_K == K && c->rec_valid >= C;
-    const int nseg = std::max(K - 1, 0);
-    std::vector<void*> ckpt(C, nullptr), seg(nseg, nullptr);
+
+    // Memory plan for the states of one segment. Flat: the segment start plus its K-1 states.
+    // Two-level: sub-checkpoints every K2 steps of the segment plus the K2-1 states of one
+    // sub-segment, i.e. ceil(K/K2) + K2 - 1 buffers, at the price of a second recompute.
+    size_t fr = 0, tot = 0;
+    LBM_CUDA(c, cudaMemGetInfo(&fr, &tot));
+    size_t avail = fr > ((size_t)1 << 30) ? fr - ((size_t)1 << 30) : 0;
+    if (c->opt.adjoint_mem_limit) avail = std::min(avail, c->opt.adjoint_mem_limit);
+    const long long mbuf = (long long)(avail / SB);
+    auto need = [&](int k2) -> long long { return k2 >= K ? K : (K + k2 - 1) / k2 + k2 - 1; };
+    int K2 = K;
+    if (need(K) > mbuf) {
+        long long best = -1;
+        for (int k2 = 1; k2 < K; ++k2)
+            if (best < 0 || need(k2) < best) {
+                best = need(k2);
+                K2 = k2;
+            }
+        if (best > mbuf)
+            return fail(c, LBM_ERR_OOM, "adjoint: segment of %d steps needs %lld states of %zu bytes, %lld fit", K,
+                        best, SB, mbuf);
+    }
+    const int S2 = (K + K2 - 1) / K2;
+    const int nbuf = (int)std::max<long long>(2, need(K2));
+
+    std::vector<void*> bufs(nbuf, nullptr), ckpt(C, nullptr);
     std::vector<bool> ckpt_host(C, false);
-    void* base = nullptr;    // device copy of a host checkpoint (segment start)
-    void* fwd[2] = {nullptr, nullptr};
     std::vector<void*> own;  // checkpoints this call allocated
     std::vector<bool> own_host;
     auto release = [&]() {
@@ -754,10 +784,7 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
             else
                 dev_free(c, own[k], SB);
         }
-        for (void* p : seg) dev_free(c, p, SB);
-        dev_free(c, base, SB);
-        dev_free(c, fwd[0], SB);
-        dev_free(c, fwd[1], SB);
+        for (void* p : bufs) dev_free(c, p, SB);
     };
     int rc = LBM_OK;
 #define LBM_ADJ_CHECK(expr, what)          \
@@ -769,16 +796,14 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
             return rc;                     \
         }                                  \
     } while (0)
-#define LBM_ADJ_ALLOC(ptr, what)                                      \
-    do {                                                              \
-        if (!((ptr) = dev_alloc(c, SB))) {                            \
-            release();                                                \
-            return fail(c, LBM_ERR_OOM, "adjoint: %s (%zu bytes)", what, SB); \
-        }                                                             \
-    } while (0)
-
-    for (int k = 0; k < nseg; ++k) LBM_ADJ_ALLOC(seg[k], "segment state");
-    LBM_ADJ_ALLOC(base, "segment start");
+    for (int k = 0; k < nbuf; ++k) {
+        if (!(bufs[k] = dev_alloc(c, SB))) {
+            release();
+            return fail(c, LBM_ERR_OOM, "adjoint: segment state %d of %d (%zu bytes)", k, nbuf, SB);
+        }
+        // solid-cell slots that no kernel writes stay defined
+        LBM_ADJ_CHECK(cudaMemsetAsync(bufs[k], 0, SB, c->stream), "clear");
+    }
     const void* cf = c->coef();
     auto step_oop = [&](const void* src, void* dst, long long t) -> cudaError_t {
         c->launches += 1;
@@ -792,22 +817,19 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
             ckpt_host[k] = c->rec_host[k];
         }
     } else {
-        // Forward pass from the initial fields, keeping the state at multiples of K.
-        size_t limit = c->opt.adjoint_mem_limit;
-        size_t fr = 0, tot = 0;
-        if (limit == 0) {
-            LBM_ADJ_CHECK(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
-            limit = fr > ((size_t)2 << 30) ? fr - ((size_t)2 << 30) : 0;
-        }
+        // Forward pass from the initial fields, keeping the state at multiples of K (device while
+        // it fits next to the segment buffers, pinned host memory beyond).
+        LBM_ADJ_CHECK(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
+        long long room = (long long)(fr > ((size_t)1 << 30) ? (fr - ((size_t)1 << 30)) / SB : 0);
         for (int k = 0; k < C; ++k) {
             void* p = nullptr;
             bool h = false;
-            if ((size_t)(k + 1) * SB <= limit) p = dev_alloc(c, SB);
+            if (room > 0 && (p = dev_alloc(c, SB))) --room;
             if (!p) {
                 if (cudaMallocHost(&p, SB) != cudaSuccess) {
                     (void)cudaGetLastError();
                     release();
-                    return fail(c, LBM_ERR_OOM, "adjoint checkpoint %d", k);
+                    return fail(c, LBM_ERR_OOM, "adjoint checkpoint %d (%zu bytes, host)", k, SB);
                 }
                 h = true;
             }
@@ -816,55 +838,80 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
             own.push_back(p);
             own_host.push_back(h);
         }
-        LBM_ADJ_ALLOC(fwd[0], "forward buffer");
-        LBM_ADJ_ALLOC(fwd[1], "forward buffer");
         const int init_layout = c->scheme == LBM_PULL2 ? LAYOUT_PULL : LAYOUT_LOCAL;
-        LBM_ADJ_CHECK(cudaMemsetAsync(fwd[0], 0, SB, c->stream), "clear");
-        LBM_ADJ_CHECK(cudaMemsetAsync(fwd[1], 0, SB, c->stream), "clear");
         LBM_ADJ_CHECK(c->ops->init(c->geom, cf, init_layout, c->rho_init_null ? nullptr : c->rho_init,
-                                   c->u_init_null ? nullptr : c->u_init, fwd[0], c->stream),
+                                   c->u_init_null ? nullptr : c->u_init, bufs[0], c->stream),
                       "adjoint init");
         c->launches += 1;
         int sb = 0;
         for (long long t = 0; t < n; ++t) {
             if (t % K == 0)
-                LBM_ADJ_CHECK(cudaMemcpyAsync(ckpt[t / K], fwd[sb], SB, cudaMemcpyDefault, c->stream),
+                LBM_ADJ_CHECK(cudaMemcpyAsync(ckpt[t / K], bufs[sb], SB, cudaMemcpyDefault, c->stream),
                               "checkpoint copy");
-            LBM_ADJ_CHECK(step_oop(fwd[sb], fwd[sb ^ 1], t), "forward recompute");
+            LBM_ADJ_CHECK(step_oop(bufs[sb], bufs[sb ^ 1], t), "forward recompute");
             sb ^= 1;
         }
-        dev_free(c, fwd[0], SB);
-        dev_free(c, fwd[1], SB);
-        fwd[0] = fwd[1] = nullptr;
     }
-    // solid-cell slots of the recompute buffers are never written; keep them defined
-    for (int k = 0; k < nseg; ++k) LBM_ADJ_CHECK(cudaMemsetAsync(seg[k], 0, SB, c->stream), "clear");
 
     // Seed from f(n), the context's current state.
     int lc = 0;
     LBM_ADJ_CHECK(c->ops->adj_seed(c->geom, cf, layout_now(c, n), state_ptr(c), loss_grad, c->lam[lc], c->stream),
                   "adjoint seed");
     c->launches += 1;
-    // Reverse sweep over segments: recompute states t0+1 .. t0+len-1, then len adjoint steps.
+    // adjoint steps t1+len-1 .. t1 over states held in st[0..len-1]
+    auto sweep = [&](const std::vector<const void*>& st, long long t1) -> cudaError_t {
+        for (int j = (int)st.size() - 1; j >= 0; --j) {
+            cudaError_t e = c->ops->adj_step(c->geom, cf, layout_now(c, t1 + j), st[j], c->lam[lc], c->lam[lc ^ 1],
+                                             c->gpart, c->stream);
+            c->launches += 1;
+            lc ^= 1;
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    // Reverse sweep over segments.
     for (int s = C - 1; s >= 0; --s) {
         const long long t0 = (long long)s * K;
         const int len = (int)std::min<long long>(K, n - t0);
         const void* start = ckpt[s];
         if (ckpt_host[s]) {
-            LBM_ADJ_CHECK(cudaMemcpyAsync(base, ckpt[s], SB, cudaMemcpyHostToDevice, c->stream), "checkpoint restore");
-            start = base;
+            LBM_ADJ_CHECK(cudaMemcpyAsync(bufs[0], ckpt[s], SB, cudaMemcpyHostToDevice, c->stream),
+                          "checkpoint restore");
+            start = bufs[0];
         }
-        for (int j = 1; j < len; ++j) {
-            const void* src = j == 1 ? start : seg[j - 2];
-            LBM_ADJ_CHECK(step_oop(src, seg[j - 1], t0 + j - 1), "segment recompute");
-        }
-        for (int j = len - 1; j >= 0; --j) {
-            const void* ft = j == 0 ? start : seg[j - 1];
-            LBM_ADJ_CHECK(c->ops->adj_step(c->geom, cf, layout_now(c, t0 + j), ft, c->lam[lc], c->lam[lc ^ 1],
-                                           c->gpart, c->stream),
-                          "adjoint step");
-            c->launches += 1;
-            lc ^= 1;
+        if (K2 >= K) {  // flat: states t0 + j in bufs[j], j = 1 .. len-1
+            std::vector<const void*> st(len);
+            st[0] = start;
+            for (int j = 1; j < len; ++j) {
+                LBM_ADJ_CHECK(step_oop(st[j - 1], bufs[j], t0 + j - 1), "segment recompute");
+                st[j] = bufs[j];
+            }
+            LBM_ADJ_CHECK(sweep(st, t0), "adjoint step");
+        } else {  // two-level: sub-checkpoints in bufs[1 .. S2-1], sub-segment states after them
+            std::vector<const void*> sub(S2);
+            sub[0] = start;
+            void** subseg = bufs.data() + S2;
+            const int nsub = (len + K2 - 1) / K2;
+            for (int j = 1; j < nsub; ++j) {
+                const void* cur = sub[j - 1];
+                for (int i = 1; i <= K2; ++i) {
+                    void* dst = i == K2 ? bufs[j] : subseg[i - 1];
+                    LBM_ADJ_CHECK(step_oop(cur, dst, t0 + (long long)(j - 1) * K2 + i - 1), "sub-checkpoint recompute");
+                    cur = dst;
+                }
+                sub[j] = bufs[j];
+            }
+            for (int j = nsub - 1; j >= 0; --j) {
+                const long long t1 = t0 + (long long)j * K2;
+                const int len2 = (int)std::min<long long>(K2, t0 + len - t1);
+                std::vector<const void*> st(len2);
+                st[0] = sub[j];
+                for (int i = 1; i < len2; ++i) {
+                    LBM_ADJ_CHECK(step_oop(st[i - 1], subseg[i - 1], t1 + i - 1), "segment recompute");
+                    st[i] = subseg[i - 1];
+                }
+                LBM_ADJ_CHECK(sweep(st, t1), "adjoint step");
+            }
         }
     }
     // Through f(0) = feq(rho0, u0; Theta).
@@ -877,7 +924,6 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
                   "gradient copy");
     LBM_ADJ_CHECK(cudaStreamSynchronize(c->stream), "adjoint sync");
 #undef LBM_ADJ_CHECK
-#undef LBM_ADJ_ALLOC
     if (c->d == 3) {
         for (int k = 0; k < 6; ++k) c->grad_theta[k] = c->hout[k];
     } else {
@@ -887,6 +933,7 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
     }
     c->grad_tau = c->hout[6];
     c->grads_ready = true;
+    c->last_adj_K2 = K2;
     release();
     return LBM_OK;
 }

@@ -106,3 +106,37 @@ def test_recorded_and_host_checkpoints_give_identical_gradients(scheme):
         out.append((dth, dtau, du0.cpu()))
     for dth, dtau, du0 in out[1:]:
         assert np.array_equal(dth, out[0][0]) and dtau == out[0][1] and torch.equal(du0, out[0][2])
+
+
+@pytest.mark.parametrize("scheme,recorded", [("pull", False), ("aa", True)])
+def test_two_level_segments_match_flat(scheme, recorded):
+    """When K segment states do not fit (adjoint_mem_limit), segments are recomputed in two
+    levels (sub-checkpoints every K2 steps); the states and the kernel order are the same, so the
+    gradients are bit-identical to the flat plan."""
+    import torch
+    from paper_2605_27004_gb300 import lbm
+    q, dims, steps, K = 27, (18, 12, 10), 29, 12
+    N = int(np.prod(dims))
+    Th = rand_theta(95, 3, 0.03)
+    solid = inputs.random_mask(N, 0.15, 96)
+    rho0, u0 = inputs.noise_field(N, 3, 0.04, 97, rho_amp=0.01)
+    u0 *= (1 - solid)[None, :]
+    g = torch.as_tensor(np.random.default_rng(98).standard_normal((3, N)) * (1 - solid)[None, :], dtype=torch.float32)
+    SB = q * N * 4
+    out = []
+    for limit in (0, 6 * SB):
+        L = lbm.LBM(q, *dims, 0.7, Th, solid=solid, storage="fp32", scheme=scheme, adjoint_mem_limit=limit)
+        if recorded:
+            L.record_checkpoints(K)
+        L.init(torch.as_tensor(rho0), torch.as_tensor(u0))
+        L.step(steps)
+        L.adjoint(g, steps, K)
+        dth, dtau, du0 = L.gradients()
+        out.append((dth, dtau, du0.cpu()))
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1] and torch.equal(out[0][2], out[1][2])
+    with pytest.raises(lbm.LBMError) as e:   # even the two-level plan needs 6 states for K = 12
+        L = lbm.LBM(q, *dims, 0.7, Th, solid=solid, storage="fp32", scheme=scheme, adjoint_mem_limit=5 * SB)
+        L.init(torch.as_tensor(rho0), torch.as_tensor(u0))
+        L.step(steps)
+        L.adjoint(g, steps, K)
+    assert e.value.status == -4
