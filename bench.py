@@ -49,6 +49,17 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def host_mem_available() -> float:
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return float(line.split()[1]) * 1024.0
+    except OSError:
+        pass
+    return 0.0
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -311,10 +322,22 @@ def run_sweep(args, torch, lbm):
         print(json.dumps(r), flush=True)
         torch.cuda.empty_cache()
     for (q, n, st, sc, K, steps) in [(19, 128, "fp32", "pull", 20, 200), (19, 128, "fp16s", "pull", 20, 200),
-                                     (19, 256, "fp32", "pull", 20, 100), (19, 256, "fp16s", "aa", 20, 100)]:
+                                     (19, 256, "fp32", "pull", 20, 100), (19, 256, "fp16s", "aa", 20, 100),
+                                     (19, 512, "fp16s", "aa", 20, 200), (19, 768, "fp16s", "aa", 20, 200)]:
         if args.only and args.only not in "adj_%d_%d_%s_%s" % (q, n, st, sc):
             continue
-        ms, N, launches = time_adjoint(q, n, st, sc, steps, K, torch, lbm)
+        # checkpoints beyond device memory go to pinned host memory: check there is room
+        need_host = (steps // K) * q * n ** 3 * ELEM[st]
+        if n >= 512 and host_mem_available() < 1.2 * need_host:
+            print(json.dumps({"adjoint": True, "lattice": f"D3Q{q}", "n": n, "storage": st, "scheme": sc,
+                              "skipped": "host memory %.0f GB < %.0f GB of checkpoints" %
+                                         (host_mem_available() / 1e9, 1.2 * need_host / 1e9)}), flush=True)
+            continue
+        try:
+            ms, N, launches = time_adjoint(q, n, st, sc, steps, K, torch, lbm)
+        except Exception as e:
+            print(json.dumps({"adjoint": True, "n": n, "error": str(e)[:300]}), flush=True)
+            continue
         print(json.dumps({"adjoint": True, "lattice": f"D3Q{q}", "n": n, "storage": st, "scheme": sc, "steps": steps,
                           "checkpoint_every": K, "mlups": N * steps / (ms * 1e-3) / 1e6, "ms": ms,
                           "launches": launches}), flush=True)
