@@ -78,8 +78,10 @@ typedef struct {
     lbm_free_fn free;         /* must be set together with alloc */
     void* alloc_user;         /* passed to alloc/free */
     void* stream;             /* cudaStream_t for every launch; NULL: the legacy default stream */
-    size_t adjoint_mem_limit; /* bytes of device memory the adjoint may hold for saved states;
-                                 0: free device memory minus a 2 GiB margin */
+    size_t adjoint_mem_limit; /* bytes of device memory for saved states (checkpoints and the
+                                 states of one segment); checkpoints beyond it go to pinned host
+                                 memory, segments beyond it are recomputed in two levels;
+                                 0: free device memory minus a margin */
 } lbm_options;
 
 /* Fill *opt with the defaults (all zero except as documented above). */

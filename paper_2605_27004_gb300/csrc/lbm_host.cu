@@ -360,7 +360,9 @@ void* ckpt_slot(lbm_ctx* c, size_t k, bool* host) {
     const size_t reserve = (c->lam[0] ? 0 : 2 * LB + (size_t)c->d * c->N * c->felem) +
                            (size_t)(2 * (int)std::ceil(std::sqrt((double)c->rec_K)) + 1) * SB + ((size_t)2 << 30);
     dev_ok = dev_ok && fr >= reserve + SB;
-    if (c->opt.adjoint_mem_limit) dev_ok = dev_ok && used + SB <= c->opt.adjoint_mem_limit;
+    if (c->opt.adjoint_mem_limit)  // the limit covers checkpoints and the smallest segment plan
+        dev_ok = dev_ok && used + SB + (size_t)(2 * (int)std::ceil(std::sqrt((double)c->rec_K)) + 1) * SB <=
+                               c->opt.adjoint_mem_limit;
     void* p = nullptr;
     bool h = false;
     if (dev_ok) p = dev_alloc(c, SB);
@@ -821,6 +823,8 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
         // it fits next to the segment buffers, pinned host memory beyond).
         LBM_ADJ_CHECK(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
         long long room = (long long)(fr > ((size_t)1 << 30) ? (fr - ((size_t)1 << 30)) / SB : 0);
+        if (c->opt.adjoint_mem_limit)  // the limit covers these checkpoints and the segment buffers
+            room = std::min(room, (long long)(c->opt.adjoint_mem_limit / SB) - nbuf);
         for (int k = 0; k < C; ++k) {
             void* p = nullptr;
             bool h = false;
