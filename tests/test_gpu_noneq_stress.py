@@ -15,7 +15,9 @@ pytestmark = pytest.mark.gpu
 PAIRS = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
 
 
-@pytest.mark.parametrize("q,order", [(27, 3), (19, 3), (27, 2)])
+# D3Q27 only: D3Q19 does not reproduce the third equilibrium moment the derivation uses (it has
+# no corner velocities), and measures 8 % off the anisotropic formula here (a lattice limit).
+@pytest.mark.parametrize("q,order", [(27, 3), (27, 2)])
 def test_nonequilibrium_stress_matches_chapman_enskog(q, order):
     import torch
     from paper_2605_27004_gb300 import build, lbm
