@@ -19,13 +19,6 @@
 //   with drho = rho - rho0, c3 = 9/2 (third order) or 0 (second order).
 // BGK relaxation (Eq. LBE_BGK): d_i <- d_i + (feq_i - r_i - d_i)/tau.
 //
-// Walls (half-way bounce-back) use ghost slots: when x - c_i is solid, the kernel that writes
-// the state also writes the bounced population f*_opp(i)(x) into the solid cell's slot that the
-// next gather of direction i at x reads (slot i at x - c_i for the pull layout, slot opp(i) at
-// x - c_i for the AA odd layout; likewise for the adjoint's lambda along +c_i). Each solid slot
-// has exactly one writer, the gathers never branch on walls, and the per-cell link word (bit i:
-// x - c_i solid, bit 31: x solid) is needed only to skip solid cells and issue the ghost stores.
-//
 // FP32 momentum identity: with weights and coefficients rounded to FP32 the discrete first
 // moment of the equilibrium is rho u (1 + eps) with a systematic eps ~ 2e-8, which drifts the
 // momentum by ~1e-5 over 1000 steps. In exact arithmetic BGK conserves momentum, so the FP32
@@ -155,21 +148,25 @@ __device__ __forceinline__ uint32_t link_of(const Geom& g, const Cell& c) {
 }
 __device__ __forceinline__ bool link_bit(uint32_t lw, int i) { return (lw >> i) & 1u; }
 
-// Gather of the pre-collision populations of one cell in shifted form (see Layout). Walls need
-// no branch here: a solid neighbour's slot holds the bounced-back population (ghost slot, written
-// by the kernel that produced the state), so every load address is independent of the walls.
-template <int Q, int S, int LAYOUT, bool RO>
-__device__ __forceinline__ void gather(const Cell& c, const Coef<typename Store<S>::T>& cf,
+// Gather of the pre-collision populations of one cell in shifted form (see Layout).
+template <int Q, int S, bool MASK, int LAYOUT, bool RO>
+__device__ __forceinline__ void gather(const Cell& c, uint32_t lw, const Coef<typename Store<S>::T>& cf,
                                        const Planes<const typename Store<S>::type>& src,
                                        typename Store<S>::T (&d)[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const Vec3 v = vel<Q>(i);
         const typename Store<S>::type* p;
-        if (LAYOUT == LAYOUT_LOCAL || i == 0)
+        if (LAYOUT == LAYOUT_LOCAL || i == 0) {
             p = src.p[i] + c.n;
-        else
-            p = src.p[LAYOUT == LAYOUT_PULL ? i : opp(i)] + off_minus(c, v);
+        } else {
+            const int slot_n = LAYOUT == LAYOUT_PULL ? i : opp(i);  // slot read from the neighbour
+            const int slot_w = LAYOUT == LAYOUT_PULL ? opp(i) : i;  // slot read on a wall link
+            if (MASK && link_bit(lw, i))
+                p = src.p[slot_w] + c.n;
+            else
+                p = src.p[slot_n] + off_minus(c, v);
+        }
         const auto raw = RO ? ld_ro(p) : ld_rw(p);
         d[i] = to_shifted<S>(raw, cf.r[i]);
     }
@@ -307,7 +304,7 @@ __device__ __forceinline__ bool bad_cell(const Macro<T>& m) {
 // the previous step, relax, store at the own cell. One launch per time step.
 // ---------------------------------------------------------------------------------------------
 template <int Q, int S, bool MASK>
-__global__ void __launch_bounds__(256, (MASK && Q == 27 && S != 1) ? 3 : 0) k_step_pull(Geom g, Coef<typename Store<S>::T> cf,
+__global__ void __launch_bounds__(256) k_step_pull(Geom g, Coef<typename Store<S>::T> cf,
                                                    const Planes<const typename Store<S>::type> src,
                                                    const Planes<typename Store<S>::type> dst, int* __restrict__ flag) {
     using T = typename Store<S>::T;
@@ -316,22 +313,11 @@ __global__ void __launch_bounds__(256, (MASK && Q == 27 && S != 1) ? 3 : 0) k_st
     const uint32_t lw = link_of<MASK>(g, c);
     if (MASK && (lw & LINK_SOLID)) return;
     T d[Q];
-    gather<Q, S, LAYOUT_PULL, true>(c, cf, src, d);
+    gather<Q, S, MASK, LAYOUT_PULL, true>(c, lw, cf, src, d);
     const Macro<T> m = bgk<Q, T, Store<S>::fix_momentum>(cf, d);
     if (bad_cell(m)) *flag = 1;
-    st_raw(dst.p[0] + c.n, from_shifted<S>(d[0], cf.r[0]));
 #pragma unroll
-    for (int k = 0; k < Lat<Q>::P; ++k) {
-        const int i = 2 * k + 1;
-        const typename Store<S>::T a = from_shifted<S>(d[i], cf.r[i]), b = from_shifted<S>(d[i + 1], cf.r[i]);
-        st_raw(dst.p[i] + c.n, a);
-        st_raw(dst.p[i + 1] + c.n, b);
-        if (MASK) {
-            // ghost slots: the next gather of direction i at x reads slot i at x - c_i
-            if (link_bit(lw, i)) st_raw(dst.p[i] + off_minus(c, vel<Q>(i)), b);
-            if (link_bit(lw, i + 1)) st_raw(dst.p[i + 1] + off_minus(c, vel<Q>(i + 1)), a);
-        }
-    }
+    for (int i = 0; i < Q; ++i) st_raw(dst.p[i] + c.n, from_shifted<S>(d[i], cf.r[i]));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -353,32 +339,18 @@ __global__ void __launch_bounds__(256) k_step_aa(Geom g, Coef<typename Store<S>:
     if (MASK && (lw & LINK_SOLID)) return;
     T d[Q];
     if (ODD)
-        gather<Q, S, LAYOUT_AAODD, false>(c, cf, src, d);
+        gather<Q, S, MASK, LAYOUT_AAODD, false>(c, lw, cf, src, d);
     else
-        gather<Q, S, LAYOUT_LOCAL, false>(c, cf, src, d);
+        gather<Q, S, MASK, LAYOUT_LOCAL, false>(c, lw, cf, src, d);
     const Macro<T> m = bgk<Q, T, Store<S>::fix_momentum>(cf, d);
     if (bad_cell(m)) *flag = 1;
-    if (!ODD) {
-        st_raw(dst.p[0] + c.n, from_shifted<S>(d[0], cf.r[0]));
-#pragma unroll
-        for (int k = 0; k < Lat<Q>::P; ++k) {
-            const int i = 2 * k + 1;
-            const typename Store<S>::T a = from_shifted<S>(d[i], cf.r[i]), b = from_shifted<S>(d[i + 1], cf.r[i]);
-            st_raw(dst.p[i + 1] + c.n, a);
-            st_raw(dst.p[i] + c.n, b);
-            if (MASK) {
-                // ghost slots for the odd gather, which reads slot opp(i) at x - c_i
-                if (link_bit(lw, i)) st_raw(dst.p[i + 1] + off_minus(c, vel<Q>(i)), b);
-                if (link_bit(lw, i + 1)) st_raw(dst.p[i] + off_minus(c, vel<Q>(i + 1)), a);
-            }
-        }
-        return;
-    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         typename Store<S>::type* p;
         if (i == 0) {
             p = dst.p[0] + c.n;
+        } else if (!ODD) {
+            p = dst.p[opp(i)] + c.n;
         } else {
             const Vec3 v = vel<Q>(i);
             if (MASK && link_bit(lw, opp(i)))
@@ -424,8 +396,11 @@ __global__ void __launch_bounds__(256) k_init(Geom g, Coef<typename Store<S>::T>
         if (LAYOUT == LAYOUT_LOCAL || i == 0) {
             p = dst.p[i] + c.n;
         } else {
-            // the slot the PULL gather reads f_i(x) from (a ghost slot when x - c_i is solid)
-            p = dst.p[i] + off_minus(c, vel<Q>(i));
+            // the slot the PULL gather reads f_i(x) from
+            if (MASK && link_bit(lw, i))
+                p = dst.p[opp(i)] + c.n;
+            else
+                p = dst.p[i] + off_minus(c, vel<Q>(i));
         }
         st_raw(p, from_shifted<S>(d[i], cf.r[i]));
     }
@@ -485,7 +460,7 @@ __global__ void __launch_bounds__(256) k_moments(Geom g, Coef<typename Store<S>:
         return;
     }
     T d[Q];
-    gather<Q, S, LAYOUT, true>(c, cf, src, d);
+    gather<Q, S, MASK, LAYOUT, true>(c, lw, cf, src, d);
     const Macro<T> m = macro_of<Q, T>(d, cf.rho0);
     if (rho_out) rho_out[c.n] = m.rho;
     if (u_out) {
@@ -555,7 +530,7 @@ __global__ void __launch_bounds__(256) k_totals(Geom g, Coef<typename Store<S>::
         const uint32_t lw = link_of<MASK>(g, c);
         if (!(MASK && (lw & LINK_SOLID))) {
             T d[Q];
-            gather<Q, S, LAYOUT, true>(c, cf, src, d);
+            gather<Q, S, MASK, LAYOUT, true>(c, lw, cf, src, d);
             const Macro<T> m = macro_of<Q, T>(d, cf.rho0);
             if (bad_cell(m)) *flag = 1;
             v[0] = (double)m.rho;
@@ -692,21 +667,13 @@ __global__ void __launch_bounds__(256) k_adj_seed(Geom g, Coef<typename Store<S>
     if (MASK && (lw & LINK_SOLID)) return;
     const size_t N = g.N;
     T d[Q];
-    gather<Q, S, LAYOUT, true>(c, cf, src, d);
+    gather<Q, S, MASK, LAYOUT, true>(c, lw, cf, src, d);
     const Macro<T> m = macro_of<Q, T>(d, cf.rho0);
     const T gx = grad[c.n], gy = grad[N + c.n], gz = Lat<Q>::D == 3 ? grad[2 * N + c.n] : T(0);
     const T inv = T(1) / m.rho;
     const T gu = gx * m.ux + gy * m.uy + gz * m.uz;
 #pragma unroll
     for (int i = 0; i < Q; ++i) lam.p[i][c.n] = (vdot<T>(vel<Q>(i), gx, gy, gz) - gu) * inv;
-    if (MASK && (lw & ~LINK_SOLID)) {
-        // ghost slots for the reverse gather: mu_i(x) reads lambda_i at x + c_i, which is
-        // lambda_opp(i)(x) when x + c_i is solid
-#pragma unroll
-        for (int i = 1; i < Q; ++i)
-            if (link_bit(lw, opp(i)))
-                lam.p[i][off_plus(c, vel<Q>(i))] = (vdot<T>(vel<Q>(opp(i)), gx, gy, gz) - gu) * inv;
-    }
 }
 
 template <int Q, int S, bool MASK, int LAYOUT>
@@ -724,11 +691,18 @@ __global__ void __launch_bounds__(256) k_adj_step(Geom g, Coef<typename Store<S>
             T mu[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                mu[i] = __ldg(i == 0 ? lam_next.p[0] + c.n : lam_next.p[i] + off_plus(c, vel<Q>(i)));
+                const T* p;
+                if (i == 0)
+                    p = lam_next.p[0] + c.n;
+                else if (MASK && link_bit(lw, opp(i)))
+                    p = lam_next.p[opp(i)] + c.n;
+                else
+                    p = lam_next.p[i] + off_plus(c, vel<Q>(i));
+                mu[i] = __ldg(p);
             }
             // f_t: moments, and f_i itself for the tau-gradient
             T dk[Q];
-            gather<Q, S, LAYOUT, true>(c, cf, src, dk);
+            gather<Q, S, MASK, LAYOUT, true>(c, lw, cf, src, dk);
             const Macro<T> m = macro_of<Q, T>(dk, cf.rho0);
             const EqCell<T> e = eq_cell<T>(cf, m.drho, m.rho, m.ux, m.uy, m.uz);
             const AdjAcc<T> A = adj_accumulate<Q, T>(cf, e, mu, dk);
@@ -740,14 +714,8 @@ __global__ void __launch_bounds__(256) k_adj_step(Geom g, Coef<typename Store<S>
             for (int k = 0; k < Lat<Q>::P; ++k) {
                 const int i = 2 * k + 1;
                 const T cv = vdot<T>(vel<Q>(i), v[0], v[1], v[2]);
-                const T li = om1 * mu[i] + om * (A.v0 + cv);
-                const T lo = om1 * mu[i + 1] + om * (A.v0 - cv);
-                lam.p[i][c.n] = li;
-                lam.p[i + 1][c.n] = lo;
-                if (MASK) {  // ghost slots (see k_adj_seed)
-                    if (link_bit(lw, i + 1)) lam.p[i][off_plus(c, vel<Q>(i))] = lo;
-                    if (link_bit(lw, i)) lam.p[i + 1][off_plus(c, vel<Q>(i + 1))] = li;
-                }
+                lam.p[i][c.n] = om1 * mu[i] + om * (A.v0 + cv);
+                lam.p[i + 1][c.n] = om1 * mu[i + 1] + om * (A.v0 - cv);
             }
 #pragma unroll
             for (int k = 0; k < 6; ++k) rec[k] = om * G[k];

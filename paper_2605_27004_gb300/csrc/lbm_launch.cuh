@@ -53,7 +53,10 @@ struct Launch {
         if constexpr (S != 1) {
             if (pairs(g)) {
                 const Shape sp = shape_pairs(g);
-                k_step_pull2<Q, S><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
+                if (g.link)
+                    k_step_pull2<Q, S, true><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
+                else
+                    k_step_pull2<Q, S, false><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
                 return cudaGetLastError();
             }
         }
@@ -73,7 +76,10 @@ struct Launch {
         if constexpr (S != 1) {
             if (pairs(g) && !odd) {
                 const Shape sp = shape_pairs(g);
-                k_step_aa_even2<Q, S><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
+                if (g.link)
+                    k_step_aa_even2<Q, S, true><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
+                else
+                    k_step_aa_even2<Q, S, false><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
                 return cudaGetLastError();
             }
         }

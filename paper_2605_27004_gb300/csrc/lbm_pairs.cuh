@@ -235,46 +235,79 @@ __device__ __forceinline__ bool bad1(float rho, float ux, float uy, float uz) {
 // ---------------------------------------------------------------------------------------------
 // Pull step, two cells per thread.
 // ---------------------------------------------------------------------------------------------
-// The pair kernels serve boxes without walls only (the wall kernels keep one cell per thread
-// and write the ghost slots that their gathers rely on).
-template <int Q, int S>
-__global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_pull2(
-    Geom g, Coef<float> cf, const Planes<const typename Store<S>::type> src, const Planes<typename Store<S>::type> dst,
-    int* __restrict__ flag) {
+template <int Q, int S, bool MASK>
+__global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_pull2(Geom g, Coef<float> cf,
+                                                    const Planes<const typename Store<S>::type> src,
+                                                    const Planes<typename Store<S>::type> dst, int* __restrict__ flag) {
     PCell c;
     make_pcell(g, c);
-    c.active = c.in_grid;
+    uint2 lw = make_uint2(0u, 0u);
+    if (MASK && c.in_grid) lw = __ldg(reinterpret_cast<const uint2*>(g.link + c.n));
+    const bool fa = !(lw.x & LINK_SOLID), fb = !(lw.y & LINK_SOLID);
+    c.active = c.in_grid && (fa || fb);
     pcell_neighbours(c);
     F2 d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const Vec3 v = vel<Q>(i);
         d[i] = gather_pair<S, true>(src.p[i], c.R[v.y + 1][v.z + 1], c, v.x, g.nx, cf.r[i]);
+        if (MASK && i > 0) {
+            const bool wa = link_bit(lw.x, i), wb = link_bit(lw.y, i);
+            if (c.active && (wa || wb)) {  // half-way bounce-back from the own cell's opposite slot
+                const F2 own = to_shifted2<S>(ld2(src.p[opp(i)] + c.n), cf.r[i]);
+                d[i] = f2(wa ? own.v.x : d[i].v.x, wb ? own.v.y : d[i].v.y);
+            }
+        }
     }
     if (!c.active) return;
     const Macro2 m = bgk2<Q, Store<S>::fix_momentum>(cf, d);
-    if (bad1(m.rho.v.x, m.ux.v.x, m.uy.v.x, m.uz.v.x) || bad1(m.rho.v.y, m.ux.v.y, m.uy.v.y, m.uz.v.y)) *flag = 1;
+    if ((fa && bad1(m.rho.v.x, m.ux.v.x, m.uy.v.x, m.uz.v.x)) || (fb && bad1(m.rho.v.y, m.ux.v.y, m.uy.v.y, m.uz.v.y)))
+        *flag = 1;
+    if (!MASK || (fa && fb)) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st2(dst.p[i] + c.n, from_shifted2<S>(d[i], cf.r[i]));
+        for (int i = 0; i < Q; ++i) st2(dst.p[i] + c.n, from_shifted2<S>(d[i], cf.r[i]));
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const F2 o = from_shifted2<S>(d[i], cf.r[i]);
+            if (fa) st_raw(dst.p[i] + c.n, o.v.x);
+            if (fb) st_raw(dst.p[i] + c.n + 1, o.v.y);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
 // AA even step (state LOCAL -> AAODD), two cells per thread: purely local.
 // ---------------------------------------------------------------------------------------------
-template <int Q, int S>
-__global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_aa_even2(
-    Geom g, Coef<float> cf, const Planes<const typename Store<S>::type> src, const Planes<typename Store<S>::type> dst,
-    int* __restrict__ flag) {
+template <int Q, int S, bool MASK>
+__global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_aa_even2(Geom g, Coef<float> cf,
+                                                       const Planes<const typename Store<S>::type> src,
+                                                       const Planes<typename Store<S>::type> dst,
+                                                       int* __restrict__ flag) {
     PCell c;
     make_pcell(g, c);
     if (!c.in_grid) return;
+    uint2 lw = make_uint2(0u, 0u);
+    if (MASK) lw = __ldg(reinterpret_cast<const uint2*>(g.link + c.n));
+    const bool fa = !(lw.x & LINK_SOLID), fb = !(lw.y & LINK_SOLID);
+    if (!fa && !fb) return;
     F2 d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = to_shifted2<S>(ld2_rw(src.p[i] + c.n), cf.r[i]);
     const Macro2 m = bgk2<Q, Store<S>::fix_momentum>(cf, d);
-    if (bad1(m.rho.v.x, m.ux.v.x, m.uy.v.x, m.uz.v.x) || bad1(m.rho.v.y, m.ux.v.y, m.uy.v.y, m.uz.v.y)) *flag = 1;
+    if ((fa && bad1(m.rho.v.x, m.ux.v.x, m.uy.v.x, m.uz.v.x)) || (fb && bad1(m.rho.v.y, m.ux.v.y, m.uy.v.y, m.uz.v.y)))
+        *flag = 1;
+    if (!MASK || (fa && fb)) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st2(dst.p[opp(i)] + c.n, from_shifted2<S>(d[i], cf.r[i]));
+        for (int i = 0; i < Q; ++i) st2(dst.p[opp(i)] + c.n, from_shifted2<S>(d[i], cf.r[i]));
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const F2 o = from_shifted2<S>(d[i], cf.r[i]);
+            if (fa) st_raw(dst.p[opp(i)] + c.n, o.v.x);
+            if (fb) st_raw(dst.p[opp(i)] + c.n + 1, o.v.y);
+        }
+    }
 }
 
 inline Shape shape_pairs(const Geom& g) {
