@@ -53,10 +53,7 @@ struct Launch {
         if constexpr (S != 1) {
             if (pairs(g)) {
                 const Shape sp = shape_pairs(g);
-                if (g.link)
-                    k_step_pull2<Q, S, true><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
-                else
-                    k_step_pull2<Q, S, false><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
+                k_step_pull2<Q, S, false><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
                 return cudaGetLastError();
             }
         }
@@ -74,10 +71,10 @@ struct Launch {
         const auto a = cpl(src, g);
         const auto b = mpl(dst, g);
         if constexpr (S != 1) {
-            if (pairs(g) && !odd) {
+            if (pairs(g)) {  // no walls (see pairs())
                 const Shape sp = shape_pairs(g);
-                if (g.link)
-                    k_step_aa_even2<Q, S, true><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
+                if (odd)
+                    k_step_aa_odd2<Q, S><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
                 else
                     k_step_aa_even2<Q, S, false><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
                 return cudaGetLastError();

@@ -310,6 +310,64 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_aa_ev
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// AA odd step (state AAODD -> LOCAL), two cells per thread, boxes without walls. Gather
+// f_i(x) = A[opp i][x - c_i] as in the pull step; scatter f*_i(x) to A[i][x + c_i]. Along x the
+// targets of (x0, x0 + 1) are shifted by c_x, so a lane stores the aligned vector (x0, x0 + 1)
+// made of its own value and the neighbouring lane's value (one shuffle); lanes at a row edge
+// (or next to an inactive lane) store single elements. Every slot is written by the lane that
+// consumed the value it replaces, after the shuffle that depends on that load: in place and
+// race free.
+// ---------------------------------------------------------------------------------------------
+template <int Q, int S>
+__global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_aa_odd2(
+    Geom g, Coef<float> cf, const Planes<const typename Store<S>::type> src, const Planes<typename Store<S>::type> dst,
+    int* __restrict__ flag) {
+    PCell c;
+    make_pcell(g, c);
+    c.active = c.in_grid;
+    pcell_neighbours(c);
+    F2 d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const Vec3 v = vel<Q>(i);
+        d[i] = gather_pair<S, false>(src.p[opp(i)], c.R[v.y + 1][v.z + 1], c, v.x, g.nx, cf.r[i]);
+    }
+    Macro2 m;
+    if (c.active) {
+        m = bgk2<Q, Store<S>::fix_momentum>(cf, d);
+        if (bad1(m.rho.v.x, m.ux.v.x, m.uy.v.x, m.uz.v.x) || bad1(m.rho.v.y, m.ux.v.y, m.uy.v.y, m.uz.v.y)) *flag = 1;
+    }
+    const int nx = g.nx;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const Vec3 v = vel<Q>(i);
+        const F2 o = from_shifted2<S>(d[i], cf.r[i]);
+        typename Store<S>::type* row = dst.p[i] + c.R[1 - v.y][1 - v.z];  // row of x + c_i
+        if (v.x == 0) {
+            if (c.active) st2(row + c.x0, o);
+        } else if (v.x == 1) {  // targets x0 + 1 (A) and x0 + 2 (B)
+            const float prevB = __shfl_up_sync(FULL, o.v.y, 1);
+            if (c.active) {
+                if (c.prev_ok)
+                    st2(row + c.x0, f2(prevB, o.v.x));
+                else
+                    st_raw(row + c.x0 + 1, o.v.x);
+                if (!c.next_ok) st_raw(row + (c.x0 + 2 == nx ? 0 : c.x0 + 2), o.v.y);
+            }
+        } else {  // targets x0 - 1 (A) and x0 (B)
+            const float nextA = __shfl_down_sync(FULL, o.v.x, 1);
+            if (c.active) {
+                if (c.next_ok)
+                    st2(row + c.x0, f2(o.v.y, nextA));
+                else
+                    st_raw(row + c.x0, o.v.y);
+                if (!c.prev_ok) st_raw(row + (c.x0 == 0 ? nx - 1 : c.x0 - 1), o.v.x);
+            }
+        }
+    }
+}
+
 inline Shape shape_pairs(const Geom& g) {
     Shape s;
     const int np = g.nx / 2;
