@@ -191,8 +191,10 @@ def test_error_paths():
     assert e.value.status == -6
 
 
+# nx multiples of 128 reach the staged-copy kernel of FP16 storage (ragged ny: the last tile
+# holds fewer than 4 rows; nx = 128 is a single tile per row, so both x halos wrap)
 PAIR_GEOMS = [(19, (2, 5, 4)), (19, (64, 3, 3)), (19, (130, 3, 2)), (19, (46, 13, 9)), (27, (38, 11, 10)),
-              (9, (98, 21, 1)), (19, (45, 7, 6))]
+              (9, (98, 21, 1)), (19, (45, 7, 6)), (19, (128, 7, 5)), (27, (256, 5, 3)), (9, (384, 9, 1))]
 
 
 @pytest.mark.parametrize("q,dims", PAIR_GEOMS)
