@@ -67,6 +67,12 @@ def _load():
             lib.oracle_threads.restype = I
             lib.oracle_collide_cell.argtypes = [I, D, P, I, P, P]
             lib.oracle_collide_cell.restype = I
+            lib.oracle_ade_init.argtypes = [I, I, I, I, P, I, P, P, P, P]
+            lib.oracle_ade_init.restype = I
+            lib.oracle_ade_run.argtypes = [I, I, I, I, D, P, I, P, P, P, I]
+            lib.oracle_ade_run.restype = I
+            lib.oracle_ade_scalar.argtypes = [I, I, I, I, P, P, P]
+            lib.oracle_ade_scalar.restype = I
             for fn in ("oracle_lattice", "oracle_feq", "oracle_init", "oracle_run", "oracle_moments",
                        "oracle_totals", "oracle_adjoint"):
                 getattr(lib, fn).restype = I
@@ -203,3 +209,33 @@ class Problem:
         self.run(f, nsteps)
         rho, u, Pi = self.moments(f)
         return f, rho, u, Pi
+
+
+class ADEProblem(Problem):
+    """Anisotropic advection-diffusion of a scalar phi by a fixed velocity field u (see
+    oracle_ade_run): same lattice, equilibrium and streaming as the flow problem."""
+
+    def __init__(self, q, nx, ny, nz, tau, Theta, u, solid=None, order=3):
+        super().__init__(q, nx, ny, nz, tau, Theta, solid=solid, order=order)
+        self.u = _f64(np.asarray(u)).reshape(self.d, self.N)
+
+    def init_scalar(self, phi):
+        g = np.zeros((self.N, self.q))
+        rc = _load().oracle_ade_init(self.q, self.nx, self.ny, self.nz, _ptr(self.Theta), self.order,
+                                     _ptr(self.solid), _ptr(_f64(phi).reshape(-1)), _ptr(self.u), _ptr(g))
+        if rc:
+            raise RuntimeError("oracle_ade_init failed")
+        return g
+
+    def run_scalar(self, g, nsteps):
+        assert g.dtype == np.float64 and g.flags.c_contiguous and g.shape == (self.N, self.q)
+        rc = _load().oracle_ade_run(self.q, self.nx, self.ny, self.nz, self.tau, _ptr(self.Theta), self.order,
+                                    _ptr(self.solid), _ptr(self.u), _ptr(g), int(nsteps))
+        if rc:
+            raise RuntimeError("oracle_ade_run failed")
+        return g
+
+    def scalar(self, g):
+        phi = np.zeros(self.N)
+        _load().oracle_ade_scalar(self.q, self.nx, self.ny, self.nz, _ptr(self.solid), _ptr(g), _ptr(phi))
+        return phi

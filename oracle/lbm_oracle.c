@@ -578,6 +578,79 @@ int oracle_adjoint(int q, int nx, int ny, int nz, double tau, const double* Thet
     return 0;
 }
 
+/* ---------------------------------------------------------------------------------------------
+ * Anisotropic advection-diffusion (the transfer named in Sec. 1 and Sec. 5; the paper gives no
+ * equations). A scalar phi carried by a prescribed velocity field u(x) has populations g_i with
+ * the equilibrium of Eq. (3rd_order_equilibrium) taken with rho -> phi:
+ *   sum geq = phi, sum geq c = phi u, sum geq c c = phi (Theta + u u),
+ * relaxed by BGK and streamed as in oracle_run (push, half-way bounce-back at solid cells).
+ * Chapman-Enskog (as in Sec. 3) then gives d_t phi + div(phi u) = div((tau - 1/2) Theta grad phi).
+ * g is [N][q] in the oracle's order; u is [d][N] and stays fixed.
+ * Pinned by: mass conservation, uniform fixed point, and the exact linear decay rate of a
+ * diffusing mode against the linearised step and the anisotropic diffusion rate.
+ * ------------------------------------------------------------------------------------------- */
+int oracle_ade_init(int q, int nx, int ny, int nz, const double* Theta, int order, const uint8_t* solid,
+                    const double* phi, const double* u, double* g) {
+    return oracle_init(q, nx, ny, nz, Theta, order, solid, phi, u, g);
+}
+
+int oracle_ade_run(int q, int nx, int ny, int nz, double tau, const double* Theta, int order, const uint8_t* solid,
+                   const double* u, double* g, int nsteps) {
+    olat L;
+    if (build_lattice(q, &L)) return -1;
+    double Kt[3][3];
+    ktilde(&L, Theta, Kt);
+    const int64_t N = (int64_t)nx * ny * nz;
+    const int qq = L.q;
+    double* h = (double*)calloc((size_t)N * qq, sizeof(double));
+    if (!h) return -2;
+    double* a = g;
+    double* b = h;
+    for (int s = 0; s < nsteps; ++s) {
+        memset(b, 0, (size_t)N * qq * sizeof(double));
+#pragma omp parallel for schedule(static)
+        for (int64_t n = 0; n < N; ++n) {
+            if (is_solid(solid, n)) continue;
+            int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((int64_t)nx * ny));
+            const double* gc = a + n * qq;
+            double phi = 0.0;
+            for (int i = 0; i < qq; ++i) phi += gc[i];
+            double u3[3] = {0, 0, 0};
+            for (int d = 0; d < L.d; ++d) u3[d] = u[(int64_t)d * N + n];
+            double geq[MAXQ];
+            feq_cell(&L, order, phi, u3, Kt, geq);
+            for (int i = 0; i < qq; ++i) {
+                double gs = gc[i] + (geq[i] - gc[i]) / tau;
+                int64_t m = neighbour(nx, ny, nz, x, y, z, L.c[i][0], L.c[i][1], L.c[i][2]);
+                if (!is_solid(solid, m))
+                    b[m * qq + i] = gs;
+                else
+                    b[n * qq + L.opp[i]] = gs;
+            }
+        }
+        double* t = a;
+        a = b;
+        b = t;
+    }
+    if (a != g) memcpy(g, a, (size_t)N * qq * sizeof(double));
+    free(h);
+    return 0;
+}
+
+/* phi = sum_i g_i per cell (0 at solid cells). */
+int oracle_ade_scalar(int q, int nx, int ny, int nz, const uint8_t* solid, const double* g, double* phi) {
+    olat L;
+    if (build_lattice(q, &L)) return -1;
+    const int64_t N = (int64_t)nx * ny * nz;
+    for (int64_t n = 0; n < N; ++n) {
+        double s = 0.0;
+        if (!is_solid(solid, n))
+            for (int i = 0; i < L.q; ++i) s += g[n * L.q + i];
+        phi[n] = s;
+    }
+    return 0;
+}
+
 /* Number of OpenMP threads the oracle runs with (1 when built without OpenMP). */
 #ifdef _OPENMP
 #include <omp.h>

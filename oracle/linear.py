@@ -110,3 +110,31 @@ def ce_shear_rate(Theta, tau, k):
     k = np.asarray(k, dtype=np.float64)
     Theta = np.asarray(Theta, dtype=np.float64).reshape(k.size, k.size)
     return float((tau - 0.5) * k @ Theta @ k)
+
+
+def ade_amplification(q, Theta, tau, k, order=3, u=None):
+    """One-step Fourier multiplier of the advection-diffusion scheme (oracle_ade_run) with a
+    uniform advecting velocity u. The map is linear in g (u is prescribed and geq is linear in
+    phi: geq(phi, u) = phi geq(1, u)), so this is exact, not a linearisation:
+    G(k) = diag(exp(-i k.c_i)) [(1 - 1/tau) I + (1/tau) e 1^T] with e = geq(1, u)."""
+    c, _, _ = _lattice(q)
+    d = D_OF_Q[q]
+    Theta = np.asarray(Theta, dtype=np.float64).reshape(d, d)
+    u = np.zeros(d) if u is None else np.asarray(u, dtype=np.float64).reshape(d)
+    e = _feq(q, 1.0, u, Theta, order)
+    om = 1.0 / tau
+    J = (1.0 - om) * np.eye(q) + om * np.outer(e, np.ones(q))
+    k = np.asarray(k, dtype=np.float64).reshape(d)
+    return np.exp(-1j * (c[:, :d] @ k))[:, None] * J
+
+
+def ade_decay_rate(q, Theta, tau, k, order=3, u=None):
+    """Decay rate per step of the slowest (diffusive) eigenmode."""
+    lam = np.linalg.eigvals(ade_amplification(q, Theta, tau, k, order, u))
+    return float(-np.log(np.abs(lam).max()))
+
+
+def ade_ce_rate(Theta, tau, k):
+    """Anisotropic diffusion rate (tau - 1/2) k.Theta.k of the Chapman-Enskog limit."""
+    k = np.asarray(k, dtype=np.float64)
+    return float((tau - 0.5) * k @ np.asarray(Theta).reshape(k.size, k.size) @ k)
