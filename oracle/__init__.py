@@ -71,6 +71,8 @@ def _load():
             lib.oracle_ade_init.restype = I
             lib.oracle_ade_run.argtypes = [I, I, I, I, D, P, I, P, P, P, I]
             lib.oracle_ade_run.restype = I
+            lib.oracle_ade_collide_cell.argtypes = [I, D, P, I, P, P, P]
+            lib.oracle_ade_collide_cell.restype = I
             lib.oracle_ade_scalar.argtypes = [I, I, I, I, P, P, P]
             lib.oracle_ade_scalar.restype = I
             for fn in ("oracle_lattice", "oracle_feq", "oracle_init", "oracle_run", "oracle_moments",
@@ -209,6 +211,19 @@ class Problem:
         self.run(f, nsteps)
         rho, u, Pi = self.moments(f)
         return f, rho, u, Pi
+
+
+def ade_collide_cell(q: int, g, u, tau: float, Theta, order: int = 3):
+    """Post-collision scalar populations of one cell (oracle direction order) for the cell's
+    advecting velocity u (see oracle_ade_run)."""
+    d = D_OF_Q[q]
+    g = _f64(np.asarray(g).reshape(q))
+    uu = _f64(np.asarray(u).reshape(d))
+    Th = _f64(np.asarray(Theta).reshape(d, d))
+    out = np.zeros(q)
+    if _load().oracle_ade_collide_cell(q, float(tau), _ptr(Th), int(order), _ptr(g), _ptr(uu), _ptr(out)):
+        raise ValueError("oracle_ade_collide_cell failed")
+    return out
 
 
 class ADEProblem(Problem):

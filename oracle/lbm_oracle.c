@@ -637,6 +637,23 @@ int oracle_ade_run(int q, int nx, int ny, int nz, double tau, const double* Thet
     return 0;
 }
 
+/* Post-collision scalar populations of one cell (oracle order): g*_i = g_i + (geq_i(phi, u) - g_i)/tau
+ * with phi = sum_i g_i and u the cell's advecting velocity (d values). */
+int oracle_ade_collide_cell(int q, double tau, const double* Theta, int order, const double* g, const double* u,
+                            double* gs) {
+    olat L;
+    if (build_lattice(q, &L)) return -1;
+    double Kt[3][3];
+    ktilde(&L, Theta, Kt);
+    double phi = 0.0;
+    for (int i = 0; i < L.q; ++i) phi += g[i];
+    double u3[3] = {0, 0, 0}, geq[MAXQ];
+    for (int a = 0; a < L.d; ++a) u3[a] = u[a];
+    feq_cell(&L, order, phi, u3, Kt, geq);
+    for (int i = 0; i < L.q; ++i) gs[i] = g[i] + (geq[i] - g[i]) / tau;
+    return 0;
+}
+
 /* phi = sum_i g_i per cell (0 at solid cells). */
 int oracle_ade_scalar(int q, int nx, int ny, int nz, const uint8_t* solid, const double* g, double* phi) {
     olat L;

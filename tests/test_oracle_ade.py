@@ -195,3 +195,28 @@ def test_uniform_state_is_a_fixed_point():
         g0 = g.copy()
         P.run_scalar(g, 5)
         assert np.abs(g - g0).max() < 1e-14
+
+
+@pytest.mark.parametrize("q,order", [(9, 3), (19, 3), (27, 2)])
+def test_one_cell_collision_moments(q, order):
+    """g* = g + (geq - g)/tau: phi kept, flux (1 - 1/tau) j + phi u / tau, second moment
+    (1 - 1/tau) Pi + phi (Theta + u u) / tau (the equilibrium's moments are exact)."""
+    d = oracle.D_OF_Q[q]
+    c, _, _ = oracle.lattice(q)
+    cc = c[:, :d].astype(np.float64)
+    rng = np.random.default_rng(inputs.SEED_BASE + 43)
+    g = 0.05 + 0.1 * rng.random(q)
+    u = 0.06 * rng.standard_normal(d)
+    tau = 0.73
+    gs = oracle.ade_collide_cell(q, g, u, tau, _theta(d), order)
+    phi = g.sum()
+    assert abs(gs.sum() - phi) < 1e-14
+    assert np.abs(gs @ cc - ((1 - 1 / tau) * (g @ cc) + phi * u / tau)).max() < 1e-14
+    Pi = np.einsum("i,ia,ib->ab", g, cc, cc)
+    Ps = np.einsum("i,ia,ib->ab", gs, cc, cc)
+    assert np.abs(Ps - ((1 - 1 / tau) * Pi + phi * (_theta(d) + np.outer(u, u)) / tau)).max() < 1e-14
+    # one cell with periodic wrap: streaming returns every population to the cell
+    P = oracle.ADEProblem(q, 1, 1, 1, tau, _theta(d), u.reshape(d, 1), order=order)
+    gg = g.reshape(1, q).copy()
+    P.run_scalar(gg, 1)
+    assert np.abs(gg[0] - gs).max() < 1e-15
