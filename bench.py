@@ -151,6 +151,18 @@ def problem(q, n, kind):
             return (n, n, n), 0.6, theta3(), None, u0.reshape(3, -1), None
         rho0, u0 = inputs.taylor_green_3d(n, 0.02)
         return (n, n, n), 0.6, theta3(), rho0, u0, None
+    if kind == "ade":  # scalar blob in the frozen Taylor-Green field (u0 = 0.05), built on the device
+        import torch
+        k = 2 * np.pi / n
+        ax = torch.arange(n, device="cuda", dtype=torch.float32)
+        s, c = torch.sin(ax * k), torch.cos(ax * k)
+        u = torch.zeros((3, n, n, n), device="cuda", dtype=torch.float32)
+        u[0] = 0.05 * s[None, None, :] * c[None, :, None] * c[:, None, None]
+        u[1] = -0.05 * c[None, None, :] * s[None, :, None] * c[:, None, None]
+        h = (n - 1) / 2
+        r2 = (ax[None, None, :] - h) ** 2 + (ax[None, :, None] - h) ** 2 + (ax[:, None, None] - h) ** 2
+        phi = 1.0 + 0.5 * torch.exp(-r2 / (2 * (n / 12) ** 2))
+        return (n, n, n), 0.6, theta3(), phi.reshape(-1), u.reshape(3, -1), None
     if kind == "porous":
         solid = inputs.porous_spheres(n, n, n, seed=inputs.SEED_BASE + 3)
         N = n ** 3
@@ -162,8 +174,12 @@ def problem(q, n, kind):
 
 def make_ctx(q, n, storage, scheme, kind, torch, lbm, **kw):
     dims, tau, Th, rho0, u0, solid = problem(q, n, kind)
-    L = lbm.LBM(q, *dims, tau, Th, solid=solid, storage=storage, scheme=scheme, **kw)
     dt = torch.float64 if storage == "fp64" else torch.float32
+    if kind == "ade":
+        L = lbm.ADE(q, *dims, tau, Th, u=u0.to(dt), storage=storage, scheme=scheme, **kw)
+        L.init(rho0.to(dt))
+        return L, L.N
+    L = lbm.LBM(q, *dims, tau, Th, solid=solid, storage=storage, scheme=scheme, **kw)
     L.init(None if rho0 is None else torch.as_tensor(rho0, dtype=dt), torch.as_tensor(u0, dtype=dt))
     n_fluid = L.N if solid is None else int((solid == 0).sum())
     return L, n_fluid
@@ -194,7 +210,7 @@ def variant(q, n, storage, scheme, kind, steps, warmup, torch, lbm, peak):
     ms, kms, launches = time_steps(L, steps, warmup, torch)
     N = L.N
     L.close()
-    bpc = 2 * q * ELEM[storage]
+    bpc = 2 * q * ELEM[storage] + ((3 if q != 9 else 2) * (8 if storage == "fp64" else 4) if kind == "ade" else 0)
     alg = nf * bpc + (N / 8 if kind == "porous" else 0)
     gbs = alg / (kms * 1e-3) / 1e9
     return {"lattice": f"D{3 if q != 9 else 2}Q{q}", "n": n, "storage": storage, "scheme": scheme, "kind": kind,
@@ -309,6 +325,8 @@ def run_sweep(args, torch, lbm):
               (19, 256, "fp32s", "pull", "tg"), (9, 4096, "fp32", "pull", "tg"), (9, 64, "fp64", "pull", "tg")]
     cases += [(27, 512, "fp32", "pull", "porous"), (27, 512, "fp16s", "pull", "porous"),
               (27, 512, "fp16s", "aa", "porous")]
+    cases += [(19, 256, "fp32", "pull", "ade"), (19, 256, "fp16s", "pull", "ade"), (19, 256, "fp16s", "aa", "ade"),
+              (27, 256, "fp32", "pull", "ade"), (19, 512, "fp32", "pull", "ade")]
     if args.only:
         cases = [c for c in cases if args.only in "%s_%d_%s_%s_%s" % (c[0], c[1], c[2], c[3], c[4])]
     for c in cases:
@@ -347,7 +365,7 @@ def run_sweep(args, torch, lbm):
 def run_profile(args, torch, lbm):
     """Small case for ncu: --kernel fwd runs warmup + steps forward launches; --kernel adjoint
     runs one short adjoint (seed, recompute, adjoint steps)."""
-    kind = "porous" if args.porous else "tg"
+    kind = "porous" if args.porous else "ade" if args.ade else "tg"
     L, _ = make_ctx(args.lattice, args.n, args.storage, args.scheme, kind, torch, lbm, use_graphs=-1)
     if args.kernel == "fwd":
         L.step(args.warmup + args.steps)
@@ -376,6 +394,7 @@ def main():
     ap.add_argument("--scheme", default="pull")
     ap.add_argument("--kernel", default="fwd", choices=["fwd", "adjoint"])
     ap.add_argument("--porous", action="store_true")
+    ap.add_argument("--ade", action="store_true", help="profile: the scalar advection-diffusion workload")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

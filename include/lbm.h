@@ -168,6 +168,51 @@ int lbm_device_bytes(const lbm_ctx* ctx, size_t* bytes);
 /* Kernel launches issued by this context since creation (all kinds). */
 int lbm_launch_count(const lbm_ctx* ctx, long long* launches);
 
+/* ---------------------------------------------------------------------------------------------
+ * Anisotropic advection-diffusion of a scalar phi (Sec. 1 and Sec. 5 name the transfer of the
+ * anisotropic equilibrium to advection-diffusion; the paper gives no equations for it).
+ * Populations g_i with phi = sum g_i relax by BGK (Eq. LBE_BGK) towards the equilibrium of
+ * Eq. (3rd_order_equilibrium) with rho -> phi and u the PRESCRIBED advecting velocity, so
+ * sum geq = phi, sum geq c = phi u, sum geq c c = phi (Theta + u u). Only phi is conserved; the
+ * Chapman-Enskog limit (Sec. 3 with rho -> phi) is d_t phi + div(phi u) = div(D grad phi) with
+ * the anisotropic diffusion tensor D = (tau - 1/2) Theta (exact for a uniform u: the covariance
+ * of a concentration blob grows by 2 D per step). Walls (half-way bounce-back on the mask) are
+ * zero-flux boundaries.
+ *
+ * A scalar context is an lbm_ctx made by lbm_ade_create; these calls apply to it unchanged:
+ *   lbm_init(ctx, phi, NULL)  g(0) = geq(phi, u) with the current advecting velocity; phi device
+ *                             [N] or NULL (uniform rho0); u must be NULL (LBM_ERR_INVALID_ARG)
+ *   lbm_step, lbm_populations, lbm_state_bytes / lbm_get_state / lbm_set_state (a state keeps
+ *   its kind and restores only into a context of the same kind), lbm_steps_done, lbm_sync,
+ *   lbm_set_params, lbm_device_bytes, lbm_launch_count, lbm_destroy;
+ *   lbm_moments(ctx, phi, j_over_phi, Pi)  rho slot = phi; u slot = sum g c / phi (the scalar's
+ *                             total flux over phi); Pi = sum g c c;
+ *   lbm_totals(ctx, &total, flux)  total = sum phi, flux = sum g c over fluid cells; fails with
+ *                             LBM_ERR_UNSTABLE only for non-finite values (phi <= 0 is allowed).
+ * lbm_adjoint, lbm_record_checkpoints and lbm_gradients return LBM_ERR_INVALID_ARG on it.
+ * opt->rho0 is the reference phi0 of the shifted storage forms (choose it near the typical phi
+ * for FP16 storage); check_every flags non-finite phi only.
+ * ------------------------------------------------------------------------------------------- */
+
+/* Same arguments, validation and ownership as lbm_create_ex. The advecting velocity starts at 0
+ * (pure anisotropic diffusion). */
+int lbm_ade_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau, const double* Theta,
+                   const uint8_t* solid_mask, const lbm_options* opt);
+
+/* Set the advecting velocity: u = a [d][N] field (device or host, field type; copied on the
+ * context's stream, values at solid cells ignored), or u_const = d host doubles (a uniform
+ * velocity), or both NULL (u = 0, no velocity reads in the step kernel). Both non-NULL, a
+ * non-finite constant or a flow context give LBM_ERR_INVALID_ARG. Takes effect from the next
+ * lbm_step or lbm_init; the populations are kept, so the velocity may change between steps. */
+int lbm_ade_set_velocity(lbm_ctx* ctx, const void* u, const double* u_const);
+
+/* The context-owned advecting-velocity field (device [d][N], field type) for in-place updates,
+ * e.g. lbm_moments(flow_ctx, NULL, *u, NULL) of a flow context with the same field type couples
+ * the scalar to a flow without a copy. Allocates the field on first use (holding the current
+ * velocity, zeros if it was 0) and makes the step read it. The pointer stays valid until
+ * lbm_destroy; writes on other streams must be ordered before the next lbm_step. */
+int lbm_ade_velocity(lbm_ctx* ctx, void** u);
+
 /* FP64 totals of a caller-owned population array with no device allocation: for callers that
  * cannot call cudaMalloc, cudaFree or any allocating routine where they need the totals (code
  * under an external memory manager that owns every device byte, code that must not synchronise

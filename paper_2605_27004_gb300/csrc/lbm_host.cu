@@ -51,6 +51,12 @@ cudaError_t reduce_partials(const double* partials, long long nb, int width, dou
     return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void k_fill(T* __restrict__ p, long long n, T v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
 static const Ops* ops_get(int q, int storage) {
 #define LBM_PICK(Q)                              \
     switch (storage) {                           \
@@ -83,6 +89,7 @@ static double weightq(int q, int i) { return q == 9 ? hweight<9>(i) : q == 19 ? 
 using namespace lbm;
 
 struct lbm_ctx {
+    int kind = 0;  // 0: flow (lbm_create), 1: advection-diffusion of a scalar (lbm_ade_create)
     int q = 0, d = 0, nx = 0, ny = 0, nz = 0;
     long long N = 0;
     double tau = 0.0;
@@ -126,6 +133,10 @@ struct lbm_ctx {
     int last_adj_K2 = 0;  // sub-segment length of the last adjoint (== K when flat)
     double grad_theta[6] = {0};
     double grad_tau = 0.0;
+
+    // advection-diffusion: library-owned advecting velocity [d][N] (field type), used unless zero
+    void* ade_u = nullptr;
+    bool ade_u_zero = true;
 
     // graphs
     cudaGraphExec_t graph = nullptr;
@@ -294,7 +305,15 @@ void* state_ptr(lbm_ctx* c) { return c->scheme == LBM_PULL2 ? c->pop[c->cur] : c
 // One time step from the current state, on stream s. Advances cur/steps.
 cudaError_t launch_step(lbm_ctx* c, cudaStream_t s) {
     cudaError_t e;
-    if (c->scheme == LBM_PULL2) {
+    if (c->kind == 1) {
+        const void* u = c->ade_u_zero ? nullptr : c->ade_u;
+        if (c->scheme == LBM_PULL2) {
+            e = c->ops->ade_pull(c->geom, c->coef(), u, c->pop[c->cur], c->pop[c->cur ^ 1], c->flag, s);
+            c->cur ^= 1;
+        } else {
+            e = c->ops->ade_aa(c->geom, c->coef(), u, (int)(c->steps & 1), c->pop[0], c->pop[0], c->flag, s);
+        }
+    } else if (c->scheme == LBM_PULL2) {
         e = c->ops->step_pull(c->geom, c->coef(), c->pop[c->cur], c->pop[c->cur ^ 1], c->flag, s);
         c->cur ^= 1;
     } else {
@@ -394,8 +413,14 @@ int record_ckpt(lbm_ctx* c) {
 int check_flag(lbm_ctx* c) {
     LBM_CUDA(c, cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (*c->hflag) return fail(c, LBM_ERR_UNSTABLE, "a fluid cell reached rho <= 0 or a non-finite value");
+    if (*c->hflag)
+        return fail(c, LBM_ERR_UNSTABLE, c->kind == 1 ? "a fluid cell reached a non-finite scalar"
+                                                      : "a fluid cell reached rho <= 0 or a non-finite value");
     return LBM_OK;
+}
+
+int flow_only(lbm_ctx* c, const char* what) {
+    return c->kind == 1 ? fail(c, LBM_ERR_INVALID_ARG, "%s: defined for flow contexts only", what) : LBM_OK;
 }
 
 }  // namespace
@@ -470,6 +495,7 @@ void lbm_destroy(lbm_ctx* c) {
     dev_free(c, c->lam[1], LB);
     dev_free(c, c->du0, (size_t)c->d * c->N * c->felem);
     dev_free(c, c->gpart, (size_t)c->shape.nblocks * 8 * sizeof(double));
+    dev_free(c, c->ade_u, (size_t)c->d * c->N * c->felem);
     if (c->hout) cudaFreeHost(c->hout);
     if (c->hflag) cudaFreeHost(c->hflag);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -608,6 +634,8 @@ int lbm_set_params(lbm_ctx* c, double tau, const double* Theta) {
 
 int lbm_init(lbm_ctx* c, const void* rho, const void* u) {
     if (!c) return LBM_ERR_INVALID_ARG;
+    if (c->kind == 1 && u)
+        return fail(c, LBM_ERR_INVALID_ARG, "lbm_init of a scalar context takes u = NULL (the advecting velocity)");
     const size_t FN = (size_t)c->N * c->felem;
     if (!c->rho_init) c->rho_init = dev_alloc(c, FN);
     if (!c->u_init) c->u_init = dev_alloc(c, FN * c->d);
@@ -619,8 +647,8 @@ int lbm_init(lbm_ctx* c, const void* rho, const void* u) {
     c->cur = 0;
     c->steps = 0;
     const int layout = c->scheme == LBM_PULL2 ? LAYOUT_PULL : LAYOUT_LOCAL;
-    cudaError_t e = c->ops->init(c->geom, c->coef(), layout, rho ? c->rho_init : nullptr, u ? c->u_init : nullptr,
-                                 c->pop[0], c->stream);
+    const void* ui = u ? c->u_init : (c->kind == 1 && !c->ade_u_zero ? c->ade_u : nullptr);
+    cudaError_t e = c->ops->init(c->geom, c->coef(), layout, rho ? c->rho_init : nullptr, ui, c->pop[0], c->stream);
     c->launches += 1;
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     LBM_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
@@ -633,6 +661,7 @@ int lbm_init(lbm_ctx* c, const void* rho, const void* u) {
 
 int lbm_record_checkpoints(lbm_ctx* c, int checkpoint_every) {
     if (!c || checkpoint_every < 0) return LBM_ERR_INVALID_ARG;
+    if (int rc = flow_only(c, "lbm_record_checkpoints")) return rc;
     c->rec_K = checkpoint_every;
     c->rec_valid = 0;
     if (checkpoint_every > 0 && c->state_valid && c->steps == 0 && c->init_fields) return record_ckpt(c);
@@ -717,6 +746,11 @@ int lbm_totals(lbm_ctx* c, double* mass, double* momentum) {
     if (mass) *mass = c->hout[0];
     if (momentum)
         for (int a = 0; a < c->d; ++a) momentum[a] = c->hout[1 + a];
+    if (c->kind == 1) {  // a scalar may be zero or negative; only non-finite values are failures
+        for (int a = 0; a <= c->d; ++a)
+            if (!std::isfinite(c->hout[a])) return fail(c, LBM_ERR_UNSTABLE, "a non-finite scalar total");
+        return LBM_OK;
+    }
     if (c->hflag[1]) return fail(c, LBM_ERR_UNSTABLE, "a fluid cell has rho <= 0 or a non-finite moment");
     return LBM_OK;
 }
@@ -727,6 +761,7 @@ int lbm_totals(lbm_ctx* c, double* mass, double* momentum) {
 // ---------------------------------------------------------------------------------------------
 int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
     if (!c || !loss_grad || n < 0 || K < 0) return LBM_ERR_INVALID_ARG;
+    if (int rc = flow_only(c, "lbm_adjoint")) return rc;
     if (!c->init_fields || !c->state_valid || c->steps != n)
         return fail(c, LBM_ERR_NO_FORWARD, "adjoint over %d steps but %lld steps were run since lbm_init", n,
                     (long long)c->steps);
@@ -944,6 +979,7 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
 
 int lbm_gradients(lbm_ctx* c, double* dTheta, double* dtau, void* du0) {
     if (!c) return LBM_ERR_INVALID_ARG;
+    if (int rc = flow_only(c, "lbm_gradients")) return rc;
     if (!c->grads_ready) return fail(c, LBM_ERR_STATE, "lbm_gradients before a successful lbm_adjoint");
     if (dTheta)
         for (int k = 0; k < (c->d == 3 ? 6 : 3); ++k) dTheta[k] = c->grad_theta[k];
@@ -987,6 +1023,7 @@ int lbm_get_state(lbm_ctx* c, void* dst, size_t bytes) {
     h.scheme = c->scheme;
     h.order = c->order;
     h.steps = c->steps;
+    h.reserved[0] = c->kind;
     LBM_CUDA(c, cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyDefault, c->stream));
     LBM_CUDA(c, cudaMemcpyAsync((char*)dst + sizeof(h), state_ptr(c), c->state_bytes(), cudaMemcpyDefault,
                                 c->stream));
@@ -1000,7 +1037,7 @@ int lbm_set_state(lbm_ctx* c, const void* src, size_t bytes) {
     lbm_state_header h;
     LBM_CUDA(c, cudaMemcpy(&h, src, sizeof(h), cudaMemcpyDefault));
     if (std::memcmp(h.magic, "LBMSTAT", 8) != 0 || h.version != 1 || h.lattice != c->q || h.nx != c->nx ||
-        h.ny != c->ny || h.nz != c->nz || h.storage != c->storage || h.scheme != c->scheme)
+        h.ny != c->ny || h.nz != c->nz || h.storage != c->storage || h.scheme != c->scheme || h.reserved[0] != c->kind)
         return fail(c, LBM_ERR_INVALID_ARG, "state does not match this context");
     c->cur = 0;
     LBM_CUDA(c, cudaMemcpyAsync(c->pop[0], (const char*)src + sizeof(h), c->state_bytes(), cudaMemcpyDefault,
@@ -1036,6 +1073,72 @@ int lbm_device_bytes(const lbm_ctx* c, size_t* bytes) {
 int lbm_launch_count(const lbm_ctx* c, long long* launches) {
     if (!c || !launches) return LBM_ERR_INVALID_ARG;
     *launches = c->launches;
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Anisotropic advection-diffusion of a scalar (lbm_ade.cuh).
+// ---------------------------------------------------------------------------------------------
+int lbm_ade_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau, const double* Theta,
+                   const uint8_t* solid_mask, const lbm_options* opt) {
+    const int rc = lbm_create_ex(out, lattice, nx, ny, nz, tau, Theta, solid_mask, opt);
+    if (rc == LBM_OK) (*out)->kind = 1;
+    return rc;
+}
+
+static int ade_field(lbm_ctx* c) {
+    if (c->ade_u) return LBM_OK;
+    const size_t bytes = (size_t)c->d * c->N * c->felem;
+    c->ade_u = dev_alloc(c, bytes);
+    if (!c->ade_u) return fail(c, LBM_ERR_OOM, "advecting-velocity field (%zu bytes)", bytes);
+    LBM_CUDA(c, cudaMemsetAsync(c->ade_u, 0, bytes, c->stream));
+    return LBM_OK;
+}
+
+static void ade_use_field(lbm_ctx* c, bool zero) {
+    if (c->ade_u_zero != zero) drop_graph(c);  // a captured step holds the field pointer or null
+    c->ade_u_zero = zero;
+}
+
+int lbm_ade_set_velocity(lbm_ctx* c, const void* u, const double* u_const) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (c->kind != 1) return fail(c, LBM_ERR_INVALID_ARG, "lbm_ade_set_velocity: not a scalar context");
+    if (u && u_const) return fail(c, LBM_ERR_INVALID_ARG, "give either a velocity field or a constant, not both");
+    if (!u && !u_const) {
+        ade_use_field(c, true);
+        return LBM_OK;
+    }
+    if (u_const)
+        for (int a = 0; a < c->d; ++a)
+            if (!std::isfinite(u_const[a])) return fail(c, LBM_ERR_INVALID_ARG, "non-finite velocity");
+    if (int rc = ade_field(c)) return rc;
+    const size_t plane = (size_t)c->N * c->felem;
+    if (u) {
+        LBM_CUDA(c, cudaMemcpyAsync(c->ade_u, u, plane * c->d, cudaMemcpyDefault, c->stream));
+    } else {
+        for (int a = 0; a < c->d; ++a) {
+            char* p = (char*)c->ade_u + a * plane;
+            if (c->storage == LBM_FP64)
+                k_fill<double><<<4 * 152, 256, 0, c->stream>>>((double*)p, c->N, u_const[a]);
+            else
+                k_fill<float><<<4 * 152, 256, 0, c->stream>>>((float*)p, c->N, (float)u_const[a]);
+            LBM_CUDA(c, cudaGetLastError());
+            c->launches += 1;
+        }
+    }
+    ade_use_field(c, false);
+    return LBM_OK;
+}
+
+int lbm_ade_velocity(lbm_ctx* c, void** u) {
+    if (!c || !u) return LBM_ERR_INVALID_ARG;
+    *u = nullptr;
+    if (c->kind != 1) return fail(c, LBM_ERR_INVALID_ARG, "lbm_ade_velocity: not a scalar context");
+    const bool fresh = c->ade_u == nullptr;
+    if (int rc = ade_field(c)) return rc;
+    if (!fresh && c->ade_u_zero) LBM_CUDA(c, cudaMemsetAsync(c->ade_u, 0, (size_t)c->d * c->N * c->felem, c->stream));
+    ade_use_field(c, false);
+    *u = c->ade_u;
     return LBM_OK;
 }
 

@@ -64,6 +64,12 @@ struct Ops {
                             void* du0, double* gpart, cudaStream_t);
     // link words from a byte mask (device, N bytes, nonzero = solid)
     cudaError_t (*link_mask)(const Geom&, const uint8_t* solid, uint32_t* link, cudaStream_t);
+    // one advection-diffusion step (lbm_ade.cuh); u is the [d][N] advecting velocity in the
+    // field type, or null for u = 0
+    cudaError_t (*ade_pull)(const Geom&, const void* coef, const void* u, const void* src, void* dst, int* flag,
+                            cudaStream_t);
+    cudaError_t (*ade_aa)(const Geom&, const void* coef, const void* u, int odd, const void* src, void* dst,
+                          int* flag, cudaStream_t);
 };
 
 // One translation unit per (lattice, storage): lbm_ops.cu compiled with LBM_Q / LBM_S.

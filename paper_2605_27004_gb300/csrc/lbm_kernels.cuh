@@ -264,11 +264,9 @@ __device__ __forceinline__ T rest_eq(const Coef<T>& cf, const EqCell<T>& e) {
     return e.drho * cf.A[0] - T(weight<Q>(0)) * e.r45 * e.usq * T(1.0 / 3.0);
 }
 
-// BGK collision in place on shifted populations; returns the macroscopic state.
-template <int Q, typename T, bool FIX>
-__device__ __forceinline__ Macro<T> bgk(const Coef<T>& cf, T (&d)[Q]) {
-    const Macro<T> m = macro_of<Q, T>(d, cf.rho0);
-    const EqCell<T> e = eq_cell<T>(cf, m.drho, m.rho, m.ux, m.uy, m.uz);
+// d_i <- (1 - 1/tau) d_i + (feq_i - r_i)/tau for the equilibrium state e (Eq. LBE_BGK).
+template <int Q, typename T>
+__device__ __forceinline__ void relax(const Coef<T>& cf, const EqCell<T>& e, T (&d)[Q]) {
     const T om = cf.omega, om1 = T(1) - cf.omega;
     d[0] = om1 * d[0] + om * rest_eq<Q, T>(cf, e);
 #pragma unroll
@@ -278,6 +276,14 @@ __device__ __forceinline__ Macro<T> bgk(const Coef<T>& cf, T (&d)[Q]) {
         d[2 * k + 1] = om1 * d[2 * k + 1] + om * (E + O);
         d[2 * k + 2] = om1 * d[2 * k + 2] + om * (E - O);
     }
+}
+
+// BGK collision in place on shifted populations; returns the macroscopic state.
+template <int Q, typename T, bool FIX>
+__device__ __forceinline__ Macro<T> bgk(const Coef<T>& cf, T (&d)[Q]) {
+    const Macro<T> m = macro_of<Q, T>(d, cf.rho0);
+    const EqCell<T> e = eq_cell<T>(cf, m.drho, m.rho, m.ux, m.uy, m.uz);
+    relax<Q, T>(cf, e, d);
     if (FIX) {
         // post-collision momentum defect, removed along 3 w_i c_i
         T ex = -m.jx, ey = -m.jy, ez = -m.jz;
@@ -329,21 +335,9 @@ __global__ void __launch_bounds__(256) k_step_pull(Geom g, Coef<typename Store<S
 // bit of x + c_i is the bit of direction opp(i).
 // ---------------------------------------------------------------------------------------------
 template <int Q, int S, bool MASK, int ODD>
-__global__ void __launch_bounds__(256) k_step_aa(Geom g, Coef<typename Store<S>::T> cf,
-                                                 const Planes<const typename Store<S>::type> src,
-                                                 const Planes<typename Store<S>::type> dst, int* __restrict__ flag) {
-    using T = typename Store<S>::T;
-    Cell c;
-    if (!make_cell(g, c)) return;
-    const uint32_t lw = link_of<MASK>(g, c);
-    if (MASK && (lw & LINK_SOLID)) return;
-    T d[Q];
-    if (ODD)
-        gather<Q, S, MASK, LAYOUT_AAODD, false>(c, lw, cf, src, d);
-    else
-        gather<Q, S, MASK, LAYOUT_LOCAL, false>(c, lw, cf, src, d);
-    const Macro<T> m = bgk<Q, T, Store<S>::fix_momentum>(cf, d);
-    if (bad_cell(m)) *flag = 1;
+__device__ __forceinline__ void aa_store(const Cell& c, uint32_t lw, const Coef<typename Store<S>::T>& cf,
+                                         const Planes<typename Store<S>::type>& dst,
+                                         const typename Store<S>::T (&d)[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         typename Store<S>::type* p;
@@ -360,6 +354,25 @@ __global__ void __launch_bounds__(256) k_step_aa(Geom g, Coef<typename Store<S>:
         }
         st_raw(p, from_shifted<S>(d[i], cf.r[i]));
     }
+}
+
+template <int Q, int S, bool MASK, int ODD>
+__global__ void __launch_bounds__(256) k_step_aa(Geom g, Coef<typename Store<S>::T> cf,
+                                                 const Planes<const typename Store<S>::type> src,
+                                                 const Planes<typename Store<S>::type> dst, int* __restrict__ flag) {
+    using T = typename Store<S>::T;
+    Cell c;
+    if (!make_cell(g, c)) return;
+    const uint32_t lw = link_of<MASK>(g, c);
+    if (MASK && (lw & LINK_SOLID)) return;
+    T d[Q];
+    if (ODD)
+        gather<Q, S, MASK, LAYOUT_AAODD, false>(c, lw, cf, src, d);
+    else
+        gather<Q, S, MASK, LAYOUT_LOCAL, false>(c, lw, cf, src, d);
+    const Macro<T> m = bgk<Q, T, Store<S>::fix_momentum>(cf, d);
+    if (bad_cell(m)) *flag = 1;
+    aa_store<Q, S, MASK, ODD>(c, lw, cf, dst, d);
 }
 
 // ---------------------------------------------------------------------------------------------

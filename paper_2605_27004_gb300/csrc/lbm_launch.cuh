@@ -1,6 +1,7 @@
 // Host-side launchers of one (lattice, storage) pair: kernel choice (one or two cells per
 // thread), launch shapes and the dispatch over walls and layouts.
 #pragma once
+#include "lbm_ade.cuh"
 #include "lbm_kernels.cuh"
 #include "lbm_pairs.cuh"
 
@@ -159,9 +160,48 @@ struct Launch {
         return cudaGetLastError();
     }
 
+    static VelField<T> vel_field(const void* u, const Geom& g) {
+        VelField<T> v{};
+        auto p = static_cast<const T*>(u);
+        for (int a = 0; a < Lat<Q>::D; ++a) v.p[a] = p ? p + (size_t)a * g.N : nullptr;
+        return v;
+    }
+
+    static cudaError_t ade_pull(const Geom& g, const void* coef, const void* u, const void* src, void* dst, int* flag,
+                                cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        if (g.link)
+            k_ade_pull<Q, S, true><<<sh.grid, sh.block, 0, st>>>(g, cf, vel_field(u, g), cpl(src, g), mpl(dst, g), flag);
+        else
+            k_ade_pull<Q, S, false><<<sh.grid, sh.block, 0, st>>>(g, cf, vel_field(u, g), cpl(src, g), mpl(dst, g), flag);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t ade_aa(const Geom& g, const void* coef, const void* u, int odd, const void* src, void* dst,
+                              int* flag, cudaStream_t st) {
+        const Shape sh = shape_for(g);
+        const CF& cf = *static_cast<const CF*>(coef);
+        const auto v = vel_field(u, g);
+        const auto a = cpl(src, g);
+        const auto b = mpl(dst, g);
+        if (g.link) {
+            if (odd)
+                k_ade_aa<Q, S, true, 1><<<sh.grid, sh.block, 0, st>>>(g, cf, v, a, b, flag);
+            else
+                k_ade_aa<Q, S, true, 0><<<sh.grid, sh.block, 0, st>>>(g, cf, v, a, b, flag);
+        } else {
+            if (odd)
+                k_ade_aa<Q, S, false, 1><<<sh.grid, sh.block, 0, st>>>(g, cf, v, a, b, flag);
+            else
+                k_ade_aa<Q, S, false, 0><<<sh.grid, sh.block, 0, st>>>(g, cf, v, a, b, flag);
+        }
+        return cudaGetLastError();
+    }
+
     static const Ops& ops() {
         static const Ops o = {&init, &step_pull, &step_aa, &moments, &totals, &adj_seed, &adj_step, &adj_init,
-                              &link_mask};
+                              &link_mask, &ade_pull, &ade_aa};
         return o;
     }
 };

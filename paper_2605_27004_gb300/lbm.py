@@ -66,6 +66,9 @@ SIGNATURES = {
     "lbm_device_bytes": (_I, [_P, ctypes.POINTER(_S)]),
     "lbm_launch_count": (_I, [_P, ctypes.POINTER(_LL)]),
     "lbm_totals_noalloc": (_I, [_I, _I, _I, _I, _I, _P, _P, _P]),
+    "lbm_ade_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _D, _P, _P, ctypes.POINTER(lbm_options)]),
+    "lbm_ade_set_velocity": (_I, [_P, _P, _P]),
+    "lbm_ade_velocity": (_I, [_P, ctypes.POINTER(_P)]),
     "lbm_status_string": (ctypes.c_char_p, [_I]),
     "lbm_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -153,6 +156,8 @@ class _TorchAllocator:
 class LBM:
     """One simulation context (``lbm_create_ex`` ... ``lbm_destroy``)."""
 
+    _scalar = False
+
     def __init__(self, lattice, nx, ny, nz, tau, Theta, solid=None, storage="fp32", scheme="pull", order=3,
                  rho0=1.0, check_every=0, use_graphs=0, device=None, stream=None, torch_alloc=True,
                  adjoint_mem_limit=0):
@@ -191,10 +196,11 @@ class LBM:
             if mask.size != self.N:
                 raise ValueError("solid mask must have N entries")
         ctx = _P()
+        create = lib.lbm_ade_create if self._scalar else lib.lbm_create_ex
         with torch.cuda.device(self.device):
-            _check(lib.lbm_create_ex(ctypes.byref(ctx), self.q, self.nx, self.ny, self.nz, float(tau),
-                                     Th.ctypes.data_as(_P), None if mask is None else mask.ctypes.data_as(_P),
-                                     ctypes.byref(opt)))
+            _check(create(ctypes.byref(ctx), self.q, self.nx, self.ny, self.nz, float(tau),
+                          Th.ctypes.data_as(_P), None if mask is None else mask.ctypes.data_as(_P),
+                          ctypes.byref(opt)))
         self.ctx = ctx
         self._opt = opt
         self.tau = float(tau)
@@ -313,6 +319,64 @@ class LBM:
 
     def sync(self):
         _check(load().lbm_sync(self.ctx), self.ctx)
+
+
+class _FieldView:
+    """A library-owned device buffer exposed through __cuda_array_interface__ (no copy)."""
+
+    def __init__(self, ptr, shape, typestr, owner):
+        self._owner = owner  # keeps the context (and with it the buffer) alive
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 2, "strides": None}
+
+
+class ADE(LBM):
+    """Anisotropic advection-diffusion of a scalar (``lbm_ade_create``): same constructor
+    arguments as :class:`LBM` (``rho0`` is the reference phi0 of the shifted storage) plus the
+    advecting velocity ``u`` ([d, N] field, a length-d constant, or None for u = 0)."""
+
+    _scalar = True
+
+    def __init__(self, lattice, nx, ny, nz, tau, Theta, u=None, **kw):
+        super().__init__(lattice, nx, ny, nz, tau, Theta, **kw)
+        if u is not None:
+            self.set_velocity(u)
+
+    def set_velocity(self, u=None):
+        """u: [d, N] field (tensor / array), a length-d constant, or None (u = 0)."""
+        lib = load()
+        if u is None:
+            _check(lib.lbm_ade_set_velocity(self.ctx, None, None), self.ctx)
+            return
+        torch = _torch()
+        if (u.numel() if isinstance(u, torch.Tensor) else np.asarray(u).size) == self.d:
+            a = u.detach().cpu().numpy() if isinstance(u, torch.Tensor) else u
+            cst = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(self.d))
+            _check(lib.lbm_ade_set_velocity(self.ctx, None, cst.ctypes.data_as(_P)), self.ctx)
+            return
+        t = self._field(u, (self.d, self.N))
+        _check(lib.lbm_ade_set_velocity(self.ctx, _ptr(t), None), self.ctx)
+        self._keep_u = t  # copied on the context's stream
+
+    def velocity_view(self):
+        """The context-owned advecting-velocity field as a [d, N] tensor aliasing it (write into
+        it to change the velocity between steps, e.g. ``flow.moments_into(u=ade.velocity_view())``)."""
+        torch = _torch()
+        p = _P()
+        _check(load().lbm_ade_velocity(self.ctx, ctypes.byref(p)), self.ctx)
+        ts = "<f8" if self.dtype == torch.float64 else "<f4"
+        return torch.as_tensor(_FieldView(p.value, (self.d, self.N), ts, self), device=self.device)
+
+    def init(self, phi=None):
+        phi_t = self._field(phi, (self.N,))
+        _check(load().lbm_init(self.ctx, _ptr(phi_t), None), self.ctx)
+        self._keep = (phi_t,)
+
+    def scalar(self):
+        """phi(x, t) = sum_i g_i (0 at solid cells)."""
+        r = self._empty(self.N)
+        _check(load().lbm_moments(self.ctx, _ptr(r), None, None), self.ctx)
+        return r
 
 
 # ABI-named module functions (marshalling only) -------------------------------------------------

@@ -74,3 +74,22 @@ def test_create_rejects_bad_geometry(lib):
 def test_status_strings(lib):
     for code in range(-9, 1):
         assert lib.lbm_status_string(code)
+
+
+@pytest.mark.parametrize("theta,tau,code", [
+    ([[0.3, 0.1], [0.0, 0.3]], 0.8, -2),
+    ([[0.3, 0.0], [0.0, 0.3]], 0.45, -3),
+])
+def test_scalar_create_validates_like_flow(lib, theta, tau, code):
+    ctx = ctypes.c_void_p()
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    rc = lib.lbm_ade_create(ctypes.byref(ctx), 9, 8, 8, 1, tau, th.ctypes.data_as(ctypes.c_void_p), None, None)
+    assert rc == code
+    assert not ctx.value
+
+
+def test_scalar_calls_reject_null_context(lib):
+    p = ctypes.c_void_p()
+    assert lib.lbm_ade_set_velocity(None, None, None) == -1
+    assert lib.lbm_ade_velocity(None, ctypes.byref(p)) == -1
+    assert not p.value
