@@ -36,8 +36,8 @@ ELEM = {"fp32": 4, "fp32s": 4, "fp16s": 2, "fp64": 8}
 # DRAM bytes per launch from an ncu capture (profiles/), keyed by variant; used only while the
 # kernel sources hash to the recorded value (otherwise the bench reports traffic = null).
 NCU_TRAFFIC = {
-    # profiles/k_step_pull_d3q19_fp32_256.md: mean of 3 launches, 256^3, read 1.2751e9 + write 1.2208e9
-    "d3q19_fp32_pull": {"traffic_bytes": 2.4959e9, "kernel_sha": "f4fa447af7b68ba6"},
+    # profiles/k_step_pull_d3q19_fp32_256.md: mean of 3 launches, 256^3, read 1.2751e9 + write 1.2205e9
+    "d3q19_fp32_pull": {"traffic_bytes": 2.4956e9, "kernel_sha": "8d4e67856a071b95"},
 }
 
 
@@ -211,7 +211,7 @@ def variant(q, n, storage, scheme, kind, steps, warmup, torch, lbm, peak):
     N = L.N
     L.close()
     bpc = 2 * q * ELEM[storage] + ((3 if q != 9 else 2) * (8 if storage == "fp64" else 4) if kind == "ade" else 0)
-    alg = nf * bpc + (N / 8 if kind == "porous" else 0)
+    alg = nf * bpc + (4 * N if kind == "porous" else 0)  # porous: one 4-byte link word per cell
     gbs = alg / (kms * 1e-3) / 1e9
     return {"lattice": f"D{3 if q != 9 else 2}Q{q}", "n": n, "storage": storage, "scheme": scheme, "kind": kind,
             "cells": N, "fluid_cells": nf, "mlups_all": N * steps / (ms * 1e-3) / 1e6,
