@@ -10,7 +10,7 @@
 // vector (row start or end, or a neighbour pair that is entirely solid or outside the grid)
 // loads that element itself, with periodic wrap. The collision runs on (cell A, cell B) pairs
 // with the packed FP32 instructions (FFMA2 / FADD2 / FMUL2), the same operation order as the
-// one-cell kernels.
+// one-cell kernels except that 1/tau is folded into per-cell factors (see bgk2).
 #pragma once
 #include "lbm_kernels.cuh"
 
@@ -164,7 +164,11 @@ __device__ __forceinline__ F2 gather_pair(const typename Store<S>::type* p, uint
 }
 
 // ---------------------------------------------------------------------------------------------
-// Pair collision (same arithmetic as bgk<Q, float, FIX>, two cells per instruction)
+// Pair collision: the arithmetic of bgk<Q, float, FIX> on two cells per instruction, with 1/tau
+// folded into the per-cell factors (om drho, om rho, om 4.5 rho) and 2 K~.u precomputed, so that
+// the relaxed value of each population is one FFMA2 away from its pair's even/odd parts. Rounding
+// differs from the one-cell kernels in the last bits; the shorter per-pair dependency chains are
+// worth 0.745 -> 0.82 of the copy peak at 256^3 for FP16 storage (measured).
 // ---------------------------------------------------------------------------------------------
 struct Macro2 {
     F2 drho, rho, jx, jy, jz, ux, uy, uz;
@@ -196,9 +200,11 @@ __device__ __forceinline__ Macro2 bgk2(const Coef<float>& cf, F2 (&d)[Q]) {
     const F2 r45 = f2(4.5f) * m.rho;
     const F2 usq3 = usq * f2(1.0f / 3.0f);
     const F2 om = f2(cf.omega), om1 = f2(1.f - cf.omega);
+    const F2 omdrho = om * m.drho, omrho = om * m.rho, omr45 = om * r45;
+    const F2 kx2 = f2(2.f) * kx, ky2 = f2(2.f) * ky, kz2 = f2(2.f) * kz;
     {
-        const F2 feq = fma2(m.drho, f2(cf.A[0]), -(f2((float)weight<Q>(0)) * r45 * usq3));
-        d[0] = fma2(om1, d[0], om * feq);
+        const F2 feq = fma2(omdrho, f2(cf.A[0]), -(f2((float)weight<Q>(0)) * omr45 * usq3));
+        d[0] = fma2(om1, d[0], feq);
     }
 #pragma unroll
     for (int k = 0; k < Lat<Q>::P; ++k) {
@@ -206,12 +212,12 @@ __device__ __forceinline__ Macro2 bgk2(const Coef<float>& cf, F2 (&d)[Q]) {
         const Vec3 v = vel<Q>(i);
         const F2 w = f2((float)weight<Q>(i));
         const F2 uc = vdot2(v, m.ux, m.uy, m.uz);
-        const F2 qk = vdot2(v, kx, ky, kz);
-        const F2 E = fma2(m.drho, f2(cf.A[i]), w * r45 * fma2(uc, uc, -usq3));
-        const F2 cub = fma2(uc, fma2(uc, uc, -usq), -(f2(2.f) * qk));
-        const F2 O = m.rho * fma2(uc, f2(cf.B[i]), w * f2(cf.c3) * cub);
-        d[i] = fma2(om1, d[i], om * (E + O));
-        d[i + 1] = fma2(om1, d[i + 1], om * (E - O));
+        const F2 qk2 = vdot2(v, kx2, ky2, kz2);
+        const F2 E = fma2(omdrho, f2(cf.A[i]), (w * omr45) * fma2(uc, uc, -usq3));
+        const F2 cub = fma2(uc, fma2(uc, uc, -usq), -qk2);
+        const F2 O = omrho * fma2(uc, f2(cf.B[i]), f2(cf.c3 * (float)weight<Q>(i)) * cub);
+        d[i] = fma2(om1, d[i], E + O);
+        d[i + 1] = fma2(om1, d[i + 1], E - O);
     }
     if (FIX) {
         F2 ex = -m.jx, ey = -m.jy, ez = -m.jz;

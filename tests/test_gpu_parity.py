@@ -191,8 +191,9 @@ def test_error_paths():
     assert e.value.status == -6
 
 
-# nx multiples of 128 reach the staged-copy kernel of FP16 storage (ragged ny: the last tile
-# holds fewer than 4 rows; nx = 128 is a single tile per row, so both x halos wrap)
+# Geometries for the two-cells-per-thread kernels (FP16 storage, even nx): rows shorter than a
+# warp, rows of one and several warps (nx = 64, 128, 256, 384: the x wrap crosses a warp or a
+# block boundary), odd nx (one-cell fallback), ragged ny and nz = 1
 PAIR_GEOMS = [(19, (2, 5, 4)), (19, (64, 3, 3)), (19, (130, 3, 2)), (19, (46, 13, 9)), (27, (38, 11, 10)),
               (9, (98, 21, 1)), (19, (45, 7, 6)), (19, (128, 7, 5)), (27, (256, 5, 3)), (9, (384, 9, 1))]
 
