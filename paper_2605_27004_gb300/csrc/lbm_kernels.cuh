@@ -45,6 +45,7 @@ struct Store<0> {
     using T = float;
     static constexpr bool shifted = false;
     static constexpr bool fix_momentum = true;
+    static constexpr bool fold_omega = false;
 };
 template <>
 struct Store<1> {
@@ -52,6 +53,7 @@ struct Store<1> {
     using T = double;
     static constexpr bool shifted = false;
     static constexpr bool fix_momentum = false;
+    static constexpr bool fold_omega = false;
 };
 template <>
 struct Store<2> {
@@ -59,6 +61,7 @@ struct Store<2> {
     using T = float;
     static constexpr bool shifted = true;
     static constexpr bool fix_momentum = true;
+    static constexpr bool fold_omega = false;
 };
 template <>
 struct Store<3> {
@@ -66,6 +69,7 @@ struct Store<3> {
     using T = float;
     static constexpr bool shifted = true;
     static constexpr bool fix_momentum = false;  // FP16 rounding (1e-3) dwarfs the 1e-8 bias
+    static constexpr bool fold_omega = true;     // see relax()
 };
 
 // read-only (non-coherent) loads: used when the source array is not written by the kernel
@@ -265,9 +269,32 @@ __device__ __forceinline__ T rest_eq(const Coef<T>& cf, const EqCell<T>& e) {
 }
 
 // d_i <- (1 - 1/tau) d_i + (feq_i - r_i)/tau for the equilibrium state e (Eq. LBE_BGK).
-template <int Q, typename T>
+// FOLD evaluates the same expression with 1/tau folded into the per-cell factors (om drho,
+// om rho, om 4.5 rho) and 2 K~.u precomputed, which shortens the dependency chain of every
+// population; it is used where the kernel is instruction-bound (FP16 storage; measured D3Q27
+// FP16 0.66 -> 0.70 of the copy peak) and rounds differently in the last bits.
+template <int Q, typename T, bool FOLD = false>
 __device__ __forceinline__ void relax(const Coef<T>& cf, const EqCell<T>& e, T (&d)[Q]) {
     const T om = cf.omega, om1 = T(1) - cf.omega;
+    if (FOLD) {
+        const T omdrho = om * e.drho, omrho = om * e.rho, omr45 = om * e.r45;
+        const T kx2 = T(2) * e.kx, ky2 = T(2) * e.ky, kz2 = T(2) * e.kz;
+        const T usq3 = e.usq * T(1.0 / 3.0);
+        d[0] = om1 * d[0] + (omdrho * cf.A[0] - T(weight<Q>(0)) * omr45 * usq3);
+#pragma unroll
+        for (int k = 0; k < Lat<Q>::P; ++k) {
+            const int i = 2 * k + 1;
+            const Vec3 v = vel<Q>(i);
+            const T w = T(weight<Q>(i));
+            const T uc = vdot<T>(v, e.ux, e.uy, e.uz);
+            const T qk2 = vdot<T>(v, kx2, ky2, kz2);
+            const T E = omdrho * cf.A[i] + (w * omr45) * (uc * uc - usq3);
+            const T O = omrho * (uc * cf.B[i] + (w * cf.c3) * (uc * (uc * uc - e.usq) - qk2));
+            d[i] = om1 * d[i] + (E + O);
+            d[i + 1] = om1 * d[i + 1] + (E - O);
+        }
+        return;
+    }
     d[0] = om1 * d[0] + om * rest_eq<Q, T>(cf, e);
 #pragma unroll
     for (int k = 0; k < Lat<Q>::P; ++k) {
@@ -279,11 +306,11 @@ __device__ __forceinline__ void relax(const Coef<T>& cf, const EqCell<T>& e, T (
 }
 
 // BGK collision in place on shifted populations; returns the macroscopic state.
-template <int Q, typename T, bool FIX>
+template <int Q, typename T, bool FIX, bool FOLD = false>
 __device__ __forceinline__ Macro<T> bgk(const Coef<T>& cf, T (&d)[Q]) {
     const Macro<T> m = macro_of<Q, T>(d, cf.rho0);
     const EqCell<T> e = eq_cell<T>(cf, m.drho, m.rho, m.ux, m.uy, m.uz);
-    relax<Q, T>(cf, e, d);
+    relax<Q, T, FOLD>(cf, e, d);
     if (FIX) {
         // post-collision momentum defect, removed along 3 w_i c_i
         T ex = -m.jx, ey = -m.jy, ez = -m.jz;
@@ -320,7 +347,7 @@ __global__ void __launch_bounds__(256) k_step_pull(Geom g, Coef<typename Store<S
     if (MASK && (lw & LINK_SOLID)) return;
     T d[Q];
     gather<Q, S, MASK, LAYOUT_PULL, true>(c, lw, cf, src, d);
-    const Macro<T> m = bgk<Q, T, Store<S>::fix_momentum>(cf, d);
+    const Macro<T> m = bgk<Q, T, Store<S>::fix_momentum, Store<S>::fold_omega>(cf, d);
     if (bad_cell(m)) *flag = 1;
 #pragma unroll
     for (int i = 0; i < Q; ++i) st_raw(dst.p[i] + c.n, from_shifted<S>(d[i], cf.r[i]));
@@ -370,7 +397,7 @@ __global__ void __launch_bounds__(256) k_step_aa(Geom g, Coef<typename Store<S>:
         gather<Q, S, MASK, LAYOUT_AAODD, false>(c, lw, cf, src, d);
     else
         gather<Q, S, MASK, LAYOUT_LOCAL, false>(c, lw, cf, src, d);
-    const Macro<T> m = bgk<Q, T, Store<S>::fix_momentum>(cf, d);
+    const Macro<T> m = bgk<Q, T, Store<S>::fix_momentum, Store<S>::fold_omega>(cf, d);
     if (bad_cell(m)) *flag = 1;
     aa_store<Q, S, MASK, ODD>(c, lw, cf, dst, d);
 }
