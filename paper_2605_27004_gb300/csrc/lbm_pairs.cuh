@@ -1,22 +1,20 @@
 // Two-cells-per-thread forward kernels for the FP32 and FP16 storage forms (sm_100+ packed FP32).
 //
 // A thread owns the x-adjacent cells (x0, x0 + 1), x0 even, of one row; a warp owns 64
-// consecutive cells of one row (rows start at lane 0 because blocks are a multiple of 32 threads
-// wide). Every population plane is read and written as aligned 2-element vectors (half2 or
-// float2), which halves the load/store and address instructions per cell. Along x the pull
-// gather needs f(x0 - c_x) and f(x0 + 1 - c_x): for c_x = +1 the element x0 - 1 is the upper
-// half of the previous lane's vector and for c_x = -1 the element x0 + 2 is the lower half of the
-// next lane's vector, so it arrives by one warp shuffle; a lane whose neighbour lane holds no
-// vector (row start or end, or a neighbour pair that is entirely solid or outside the grid)
-// loads that element itself, with periodic wrap. The collision runs on (cell A, cell B) pairs
-// with the packed FP32 instructions (FFMA2 / FADD2 / FMUL2), the same operation order as the
-// one-cell kernels except that 1/tau is folded into per-cell factors (see bgk2).
+// consecutive cells of one row (blocks are a multiple of 32 threads wide). Population planes
+// whose velocity has c_x = 0 are read and written as aligned 2-element vectors (half2 or
+// float2), which halves their load/store and address instructions per cell. Along x the pull
+// gather needs f(x0 - c_x) and f(x0 + 1 - c_x), which straddle a vector boundary when
+// c_x = +-1; those directions are read (and the odd AA step's scatter along +c_x is written) as
+// two single elements with periodic wrap. Exchanging the straddling element with the
+// neighbouring lane by a warp shuffle instead measured 1-4 % slower. The collision runs on
+// (cell A, cell B) pairs with the packed FP32 instructions (FFMA2 / FADD2 / FMUL2), the same
+// operation order as the one-cell kernels except that 1/tau is folded into per-cell factors
+// (see bgk2).
 #pragma once
 #include "lbm_kernels.cuh"
 
 namespace lbm {
-
-constexpr unsigned FULL = 0xffffffffu;
 
 // ---------------------------------------------------------------------------------------------
 // Packed FP32 pair arithmetic
@@ -98,11 +96,9 @@ __device__ __forceinline__ F2 from_shifted2(F2 d, float r) {
 
 // Pair cell: thread (lane) owns x0 and x0 + 1 of row (y, z).
 struct PCell {
-    int x0, y, z, lane;
+    int x0, y, z;
     bool in_grid;    // the pair lies inside the grid
     bool active;     // in the grid and not entirely solid
-    bool prev_ok;    // the previous lane holds an active pair of the same row
-    bool next_ok;    // the next lane holds an active pair of the same row
     uint32_t n;      // index of cell x0
     uint32_t X[3];   // wrapped x0 + 1, x0, x0 - 1 (only X[1] is used for vector access)
     uint32_t R[3][3];
@@ -113,7 +109,6 @@ __device__ __forceinline__ void make_pcell(const Geom& g, PCell& c) {
     c.x0 = 2 * px;
     c.y = blockIdx.y * blockDim.y + threadIdx.y;
     c.z = blockIdx.z;
-    c.lane = (threadIdx.x + threadIdx.y * blockDim.x) & 31;
     c.in_grid = c.x0 < g.nx && c.y < g.ny;
     // clamp out-of-grid lanes to a valid pair so that any address they form is in bounds
     const int x0 = c.in_grid ? c.x0 : 0;
@@ -131,34 +126,19 @@ __device__ __forceinline__ void make_pcell(const Geom& g, PCell& c) {
     c.x0 = x0;
 }
 
-__device__ __forceinline__ void pcell_neighbours(PCell& c) {
-    const unsigned am = __ballot_sync(FULL, c.active);
-    c.prev_ok = c.lane > 0 && ((am >> (c.lane - 1)) & 1u) && c.x0 > 0;
-    c.next_ok = c.lane < 31 && ((am >> (c.lane + 1)) & 1u);
-}
-
 // f(x0 - cx) and f(x0 + 1 - cx) of the row at element offset `row` of plane p (pull shift).
 template <int S, bool RO>
 __device__ __forceinline__ F2 gather_pair(const typename Store<S>::type* p, uint32_t row, const PCell& c, int cx,
                                           int nx, float r) {
     F2 v = f2(0.f);
-    if (c.active) v = RO ? ld2(p + row + c.x0) : ld2_rw(p + row + c.x0);
-    if (cx == 1) {
-        const float prev = __shfl_up_sync(FULL, v.v.y, 1);
-        float a = prev;
-        if (c.active && !c.prev_ok) {
-            const int xm = c.x0 == 0 ? nx - 1 : c.x0 - 1;
-            a = RO ? ld_ro(p + row + xm) : ld_rw(p + row + xm);
+    if (c.active) {
+        if (cx == 0) {
+            v = RO ? ld2(p + row + c.x0) : ld2_rw(p + row + c.x0);
+        } else {
+            const int xa = cx == 1 ? (c.x0 == 0 ? nx - 1 : c.x0 - 1) : c.x0 + 1;
+            const int xb = cx == 1 ? c.x0 : (c.x0 + 2 == nx ? 0 : c.x0 + 2);
+            v = f2(RO ? ld_ro(p + row + xa) : ld_rw(p + row + xa), RO ? ld_ro(p + row + xb) : ld_rw(p + row + xb));
         }
-        v = f2(a, v.v.x);
-    } else if (cx == -1) {
-        const float next = __shfl_down_sync(FULL, v.v.x, 1);
-        float b = next;
-        if (c.active && !c.next_ok) {
-            const int xp = c.x0 + 2 == nx ? 0 : c.x0 + 2;
-            b = RO ? ld_ro(p + row + xp) : ld_rw(p + row + xp);
-        }
-        v = f2(v.v.y, b);
     }
     return to_shifted2<S>(v, r);
 }
@@ -251,7 +231,6 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_pull2
     if (MASK && c.in_grid) lw = __ldg(reinterpret_cast<const uint2*>(g.link + c.n));
     const bool fa = !(lw.x & LINK_SOLID), fb = !(lw.y & LINK_SOLID);
     c.active = c.in_grid && (fa || fb);
-    pcell_neighbours(c);
     F2 d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -319,11 +298,13 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_aa_ev
 // ---------------------------------------------------------------------------------------------
 // AA odd step (state AAODD -> LOCAL), two cells per thread, boxes without walls. Gather
 // f_i(x) = A[opp i][x - c_i] as in the pull step; scatter f*_i(x) to A[i][x + c_i]. Along x the
-// targets of (x0, x0 + 1) are shifted by c_x, so a lane stores the aligned vector (x0, x0 + 1)
-// made of its own value and the neighbouring lane's value (one shuffle); lanes at a row edge
-// (or next to an inactive lane) store single elements. Every slot is written by the lane that
-// consumed the value it replaces, after the shuffle that depends on that load: in place and
-// race free.
+// targets of (x0, x0 + 1) are shifted by c_x, so those directions are stored as two single
+// elements (x0 + c_x, x0 + 1 + c_x), with periodic wrap; the others as one aligned vector.
+// The old value of slot (i, x + c_i) is the population f_opp(i)(x) of the same cell, gathered by
+// this thread; the store depends on that value through the collision, so every slot is read
+// before it is replaced, by the only thread that writes it: in place and race free. (A thread's
+// vector loads may also fetch an element that another thread consumes and replaces; such an
+// element is never used by the fetching thread.)
 // ---------------------------------------------------------------------------------------------
 template <int Q, int S>
 __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_aa_odd2(
@@ -332,7 +313,6 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_aa_od
     PCell c;
     make_pcell(g, c);
     c.active = c.in_grid;
-    pcell_neighbours(c);
     F2 d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -353,22 +333,14 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_aa_od
         if (v.x == 0) {
             if (c.active) st2(row + c.x0, o);
         } else if (v.x == 1) {  // targets x0 + 1 (A) and x0 + 2 (B)
-            const float prevB = __shfl_up_sync(FULL, o.v.y, 1);
             if (c.active) {
-                if (c.prev_ok)
-                    st2(row + c.x0, f2(prevB, o.v.x));
-                else
-                    st_raw(row + c.x0 + 1, o.v.x);
-                if (!c.next_ok) st_raw(row + (c.x0 + 2 == nx ? 0 : c.x0 + 2), o.v.y);
+                st_raw(row + c.x0 + 1, o.v.x);
+                st_raw(row + (c.x0 + 2 == nx ? 0 : c.x0 + 2), o.v.y);
             }
         } else {  // targets x0 - 1 (A) and x0 (B)
-            const float nextA = __shfl_down_sync(FULL, o.v.x, 1);
             if (c.active) {
-                if (c.next_ok)
-                    st2(row + c.x0, f2(o.v.y, nextA));
-                else
-                    st_raw(row + c.x0, o.v.y);
-                if (!c.prev_ok) st_raw(row + (c.x0 == 0 ? nx - 1 : c.x0 - 1), o.v.x);
+                st_raw(row + (c.x0 == 0 ? nx - 1 : c.x0 - 1), o.v.x);
+                st_raw(row + c.x0, o.v.y);
             }
         }
     }
