@@ -321,7 +321,8 @@ def run_sweep(args, torch, lbm):
     for n in (64, 128, 256, 512):
         cases += [(19, n, "fp32", "pull", "tg"), (19, n, "fp16s", "pull", "tg"), (19, n, "fp16s", "aa", "tg")]
     cases += [(19, 768, "fp16s", "aa", "tg")]
-    cases += [(27, 256, "fp32", "pull", "tg"), (27, 256, "fp16s", "pull", "tg"), (19, 256, "fp32", "aa", "tg"),
+    cases += [(27, 256, "fp32", "pull", "tg"), (27, 256, "fp16s", "pull", "tg"), (27, 256, "fp16s", "aa", "tg"),
+              (19, 256, "fp32", "aa", "tg"),
               (19, 256, "fp32s", "pull", "tg"), (9, 4096, "fp32", "pull", "tg"), (9, 64, "fp64", "pull", "tg")]
     cases += [(27, 512, "fp32", "pull", "porous"), (27, 512, "fp16s", "pull", "porous"),
               (27, 512, "fp16s", "aa", "porous")]

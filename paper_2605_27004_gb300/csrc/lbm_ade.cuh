@@ -11,7 +11,9 @@
 // storage forms and the AA pattern are those of the flow kernels.
 //
 // The velocity is a [d][N] field in the arithmetic type (float, or double for FP64 storage),
-// read once per cell, or absent (u = 0, pure anisotropic diffusion).
+// read once per cell, or absent (u = 0, pure anisotropic diffusion). These one-cell kernels
+// serve FP32 / FP64 storage and boxes with walls; FP16 storage without walls runs the scalar
+// collision in the two-cells-per-thread kernels of lbm_pairs.cuh (collide2 with ADE = true).
 #pragma once
 #include "lbm_kernels.cuh"
 

@@ -41,9 +41,10 @@ struct Launch {
     }
 
     // Two cells per thread pay off where the one-cell kernel is instruction-bound: FP16 storage
-    // without walls on D2Q9/D3Q19 (measured: 0.61 -> 0.75 of HBM bandwidth). FP32 storage is at
-    // the bandwidth bound with one cell per thread already, and the wall variants lose occupancy.
-    static bool pairs(const Geom& g) { return S == 3 && Q != 27 && !g.link && (g.nx % 2) == 0; }
+    // without walls (measured at 256^3: D3Q19 0.61 -> 0.82, D3Q27 0.70 -> 0.75 of the copy peak).
+    // FP32 storage is at the bandwidth bound with one cell per thread already, and the wall
+    // variants lose occupancy.
+    static bool pairs(const Geom& g) { return S == 3 && !g.link && (g.nx % 2) == 0; }
 
     static cudaError_t step_pull(const Geom& g, const void* coef, const void* src, void* dst, int* flag,
                                  cudaStream_t st) {
@@ -54,7 +55,7 @@ struct Launch {
         if constexpr (S != 1) {
             if (pairs(g)) {
                 const Shape sp = shape_pairs(g);
-                k_step_pull2<Q, S, false><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
+                k_step_pull2<Q, S, false><<<sp.grid, sp.block, 0, st>>>(g, cf, VelField<float>{}, a, b, flag);
                 return cudaGetLastError();
             }
         }
@@ -75,9 +76,9 @@ struct Launch {
             if (pairs(g)) {  // no walls (see pairs())
                 const Shape sp = shape_pairs(g);
                 if (odd)
-                    k_step_aa_odd2<Q, S><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
+                    k_step_aa_odd2<Q, S><<<sp.grid, sp.block, 0, st>>>(g, cf, VelField<float>{}, a, b, flag);
                 else
-                    k_step_aa_even2<Q, S, false><<<sp.grid, sp.block, 0, st>>>(g, cf, a, b, flag);
+                    k_step_aa_even2<Q, S, false><<<sp.grid, sp.block, 0, st>>>(g, cf, VelField<float>{}, a, b, flag);
                 return cudaGetLastError();
             }
         }
@@ -171,6 +172,14 @@ struct Launch {
                                 cudaStream_t st) {
         const Shape sh = shape_for(g);
         const CF& cf = *static_cast<const CF*>(coef);
+        if constexpr (S != 1) {
+            if (pairs(g)) {
+                const Shape sp = shape_pairs(g);
+                k_step_pull2<Q, S, false, true><<<sp.grid, sp.block, 0, st>>>(g, cf, vel_field(u, g), cpl(src, g),
+                                                                            mpl(dst, g), flag);
+                return cudaGetLastError();
+            }
+        }
         if (g.link)
             k_ade_pull<Q, S, true><<<sh.grid, sh.block, 0, st>>>(g, cf, vel_field(u, g), cpl(src, g), mpl(dst, g), flag);
         else
@@ -185,6 +194,16 @@ struct Launch {
         const auto v = vel_field(u, g);
         const auto a = cpl(src, g);
         const auto b = mpl(dst, g);
+        if constexpr (S != 1) {
+            if (pairs(g)) {
+                const Shape sp = shape_pairs(g);
+                if (odd)
+                    k_step_aa_odd2<Q, S, true><<<sp.grid, sp.block, 0, st>>>(g, cf, v, a, b, flag);
+                else
+                    k_step_aa_even2<Q, S, false, true><<<sp.grid, sp.block, 0, st>>>(g, cf, v, a, b, flag);
+                return cudaGetLastError();
+            }
+        }
         if (g.link) {
             if (odd)
                 k_ade_aa<Q, S, true, 1><<<sh.grid, sh.block, 0, st>>>(g, cf, v, a, b, flag);

@@ -12,6 +12,7 @@
 // operation order as the one-cell kernels except that 1/tau is folded into per-cell factors
 // (see bgk2).
 #pragma once
+#include "lbm_ade.cuh"
 #include "lbm_kernels.cuh"
 
 namespace lbm {
@@ -154,6 +155,38 @@ struct Macro2 {
     F2 drho, rho, jx, jy, jz, ux, uy, uz;
 };
 
+// Relaxation of a pair towards feq(rho, u) in shifted variables (drho = rho - rho0), with 1/tau
+// folded into the per-cell factors and 2 K~.u precomputed (see the file comment).
+template <int Q>
+__device__ __forceinline__ void relax2(const Coef<float>& cf, F2 drho, F2 rho, F2 ux, F2 uy, F2 uz, F2 (&d)[Q]) {
+    const F2 usq = fma2(ux, ux, fma2(uy, uy, uz * uz));
+    const F2 kx = fma2(f2(cf.K[0]), ux, fma2(f2(cf.K[3]), uy, f2(cf.K[4]) * uz));
+    const F2 ky = fma2(f2(cf.K[3]), ux, fma2(f2(cf.K[1]), uy, f2(cf.K[5]) * uz));
+    const F2 kz = fma2(f2(cf.K[4]), ux, fma2(f2(cf.K[5]), uy, f2(cf.K[2]) * uz));
+    const F2 r45 = f2(4.5f) * rho;
+    const F2 usq3 = usq * f2(1.0f / 3.0f);
+    const F2 om = f2(cf.omega), om1 = f2(1.f - cf.omega);
+    const F2 omdrho = om * drho, omrho = om * rho, omr45 = om * r45;
+    const F2 kx2 = f2(2.f) * kx, ky2 = f2(2.f) * ky, kz2 = f2(2.f) * kz;
+    {
+        const F2 feq = fma2(omdrho, f2(cf.A[0]), -(f2((float)weight<Q>(0)) * omr45 * usq3));
+        d[0] = fma2(om1, d[0], feq);
+    }
+#pragma unroll
+    for (int k = 0; k < Lat<Q>::P; ++k) {
+        const int i = 2 * k + 1;
+        const Vec3 v = vel<Q>(i);
+        const F2 w = f2((float)weight<Q>(i));
+        const F2 uc = vdot2(v, ux, uy, uz);
+        const F2 qk2 = vdot2(v, kx2, ky2, kz2);
+        const F2 E = fma2(omdrho, f2(cf.A[i]), (w * omr45) * fma2(uc, uc, -usq3));
+        const F2 cub = fma2(uc, fma2(uc, uc, -usq), -qk2);
+        const F2 O = omrho * fma2(uc, f2(cf.B[i]), f2(cf.c3 * (float)weight<Q>(i)) * cub);
+        d[i] = fma2(om1, d[i], E + O);
+        d[i + 1] = fma2(om1, d[i + 1], E - O);
+    }
+}
+
 template <int Q, bool FIX>
 __device__ __forceinline__ Macro2 bgk2(const Coef<float>& cf, F2 (&d)[Q]) {
     Macro2 m;
@@ -173,32 +206,7 @@ __device__ __forceinline__ Macro2 bgk2(const Coef<float>& cf, F2 (&d)[Q]) {
     m.ux = jx * inv;
     m.uy = jy * inv;
     m.uz = Lat<Q>::D == 3 ? jz * inv : f2(0.f);
-    const F2 usq = fma2(m.ux, m.ux, fma2(m.uy, m.uy, m.uz * m.uz));
-    const F2 kx = fma2(f2(cf.K[0]), m.ux, fma2(f2(cf.K[3]), m.uy, f2(cf.K[4]) * m.uz));
-    const F2 ky = fma2(f2(cf.K[3]), m.ux, fma2(f2(cf.K[1]), m.uy, f2(cf.K[5]) * m.uz));
-    const F2 kz = fma2(f2(cf.K[4]), m.ux, fma2(f2(cf.K[5]), m.uy, f2(cf.K[2]) * m.uz));
-    const F2 r45 = f2(4.5f) * m.rho;
-    const F2 usq3 = usq * f2(1.0f / 3.0f);
-    const F2 om = f2(cf.omega), om1 = f2(1.f - cf.omega);
-    const F2 omdrho = om * m.drho, omrho = om * m.rho, omr45 = om * r45;
-    const F2 kx2 = f2(2.f) * kx, ky2 = f2(2.f) * ky, kz2 = f2(2.f) * kz;
-    {
-        const F2 feq = fma2(omdrho, f2(cf.A[0]), -(f2((float)weight<Q>(0)) * omr45 * usq3));
-        d[0] = fma2(om1, d[0], feq);
-    }
-#pragma unroll
-    for (int k = 0; k < Lat<Q>::P; ++k) {
-        const int i = 2 * k + 1;
-        const Vec3 v = vel<Q>(i);
-        const F2 w = f2((float)weight<Q>(i));
-        const F2 uc = vdot2(v, m.ux, m.uy, m.uz);
-        const F2 qk2 = vdot2(v, kx2, ky2, kz2);
-        const F2 E = fma2(omdrho, f2(cf.A[i]), (w * omr45) * fma2(uc, uc, -usq3));
-        const F2 cub = fma2(uc, fma2(uc, uc, -usq), -qk2);
-        const F2 O = omrho * fma2(uc, f2(cf.B[i]), f2(cf.c3 * (float)weight<Q>(i)) * cub);
-        d[i] = fma2(om1, d[i], E + O);
-        d[i + 1] = fma2(om1, d[i + 1], E - O);
-    }
+    relax2<Q>(cf, m.drho, m.rho, m.ux, m.uy, m.uz, d);
     if (FIX) {
         F2 ex = -m.jx, ey = -m.jy, ez = -m.jz;
 #pragma unroll
@@ -218,13 +226,38 @@ __device__ __forceinline__ bool bad1(float rho, float ux, float uy, float uz) {
     return !(rho > 0.f) || !isfinite(ux + uy + uz);
 }
 
+// Collision of the pair at cell index n (even): the flow's BGK, or (ADE) the advection-diffusion
+// relaxation of a scalar with the prescribed velocity read as one aligned vector per component
+// (lbm_ade.cuh). Returns true when a fluid cell of the pair (fa, fb) is unstable.
+template <int Q, int S, bool ADE>
+__device__ __forceinline__ bool collide2(const Coef<float>& cf, const VelField<float>& vf, uint32_t n, F2 (&d)[Q],
+                                         bool fa, bool fb) {
+    if constexpr (ADE) {
+        F2 ux = f2(0.f), uy = f2(0.f), uz = f2(0.f);
+        if (vf.p[0] != nullptr) {
+            ux = ld2(vf.p[0] + n);
+            uy = ld2(vf.p[1] + n);
+            if (Lat<Q>::D == 3) uz = ld2(vf.p[2] + n);
+        }
+        F2 s = d[0];
+#pragma unroll
+        for (int k = 0; k < Lat<Q>::P; ++k) s += d[2 * k + 1] + d[2 * k + 2];
+        relax2<Q>(cf, s, f2(cf.rho0) + s, ux, uy, uz, d);
+        return (fa && !isfinite(s.v.x)) || (fb && !isfinite(s.v.y));
+    } else {
+        const Macro2 m = bgk2<Q, Store<S>::fix_momentum>(cf, d);
+        return (fa && bad1(m.rho.v.x, m.ux.v.x, m.uy.v.x, m.uz.v.x)) ||
+               (fb && bad1(m.rho.v.y, m.ux.v.y, m.uy.v.y, m.uz.v.y));
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Pull step, two cells per thread.
 // ---------------------------------------------------------------------------------------------
-template <int Q, int S, bool MASK>
-__global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_pull2(Geom g, Coef<float> cf,
-                                                    const Planes<const typename Store<S>::type> src,
-                                                    const Planes<typename Store<S>::type> dst, int* __restrict__ flag) {
+template <int Q, int S, bool MASK, bool ADE = false>
+__global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3)
+    k_step_pull2(Geom g, Coef<float> cf, VelField<float> vf, const Planes<const typename Store<S>::type> src,
+                 const Planes<typename Store<S>::type> dst, int* __restrict__ flag) {
     PCell c;
     make_pcell(g, c);
     uint2 lw = make_uint2(0u, 0u);
@@ -245,9 +278,7 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_pull2
         }
     }
     if (!c.active) return;
-    const Macro2 m = bgk2<Q, Store<S>::fix_momentum>(cf, d);
-    if ((fa && bad1(m.rho.v.x, m.ux.v.x, m.uy.v.x, m.uz.v.x)) || (fb && bad1(m.rho.v.y, m.ux.v.y, m.uy.v.y, m.uz.v.y)))
-        *flag = 1;
+    if (collide2<Q, S, ADE>(cf, vf, c.n, d, fa, fb)) *flag = 1;
     if (!MASK || (fa && fb)) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) st2(dst.p[i] + c.n, from_shifted2<S>(d[i], cf.r[i]));
@@ -264,11 +295,10 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_pull2
 // ---------------------------------------------------------------------------------------------
 // AA even step (state LOCAL -> AAODD), two cells per thread: purely local.
 // ---------------------------------------------------------------------------------------------
-template <int Q, int S, bool MASK>
-__global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_aa_even2(Geom g, Coef<float> cf,
-                                                       const Planes<const typename Store<S>::type> src,
-                                                       const Planes<typename Store<S>::type> dst,
-                                                       int* __restrict__ flag) {
+template <int Q, int S, bool MASK, bool ADE = false>
+__global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3)
+    k_step_aa_even2(Geom g, Coef<float> cf, VelField<float> vf, const Planes<const typename Store<S>::type> src,
+                    const Planes<typename Store<S>::type> dst, int* __restrict__ flag) {
     PCell c;
     make_pcell(g, c);
     if (!c.in_grid) return;
@@ -279,9 +309,7 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_aa_ev
     F2 d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = to_shifted2<S>(ld2_rw(src.p[i] + c.n), cf.r[i]);
-    const Macro2 m = bgk2<Q, Store<S>::fix_momentum>(cf, d);
-    if ((fa && bad1(m.rho.v.x, m.ux.v.x, m.uy.v.x, m.uz.v.x)) || (fb && bad1(m.rho.v.y, m.ux.v.y, m.uy.v.y, m.uz.v.y)))
-        *flag = 1;
+    if (collide2<Q, S, ADE>(cf, vf, c.n, d, fa, fb)) *flag = 1;
     if (!MASK || (fa && fb)) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) st2(dst.p[opp(i)] + c.n, from_shifted2<S>(d[i], cf.r[i]));
@@ -306,10 +334,10 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_aa_ev
 // vector loads may also fetch an element that another thread consumes and replaces; such an
 // element is never used by the fetching thread.)
 // ---------------------------------------------------------------------------------------------
-template <int Q, int S>
-__global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_aa_odd2(
-    Geom g, Coef<float> cf, const Planes<const typename Store<S>::type> src, const Planes<typename Store<S>::type> dst,
-    int* __restrict__ flag) {
+template <int Q, int S, bool ADE = false>
+__global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3)
+    k_step_aa_odd2(Geom g, Coef<float> cf, VelField<float> vf, const Planes<const typename Store<S>::type> src,
+                   const Planes<typename Store<S>::type> dst, int* __restrict__ flag) {
     PCell c;
     make_pcell(g, c);
     c.active = c.in_grid;
@@ -319,11 +347,7 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3) k_step_aa_od
         const Vec3 v = vel<Q>(i);
         d[i] = gather_pair<S, false>(src.p[opp(i)], c.R[v.y + 1][v.z + 1], c, v.x, g.nx, cf.r[i]);
     }
-    Macro2 m;
-    if (c.active) {
-        m = bgk2<Q, Store<S>::fix_momentum>(cf, d);
-        if (bad1(m.rho.v.x, m.ux.v.x, m.uy.v.x, m.uz.v.x) || bad1(m.rho.v.y, m.ux.v.y, m.uy.v.y, m.uz.v.y)) *flag = 1;
-    }
+    if (c.active && collide2<Q, S, ADE>(cf, vf, c.n, d, true, true)) *flag = 1;
     const int nx = g.nx;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
