@@ -220,21 +220,27 @@ def variant(q, n, storage, scheme, kind, steps, warmup, torch, lbm, peak):
 
 
 def time_adjoint(q, n, storage, scheme, steps, K, torch, lbm):
-    """Wall time of lbm_adjoint through `steps` steps (forward recompute + reverse sweep)."""
+    """Wall time of lbm_adjoint through `steps` steps (forward recompute + reverse sweep), in
+    steady state: the second of two calls on the same forward run, as in an optimisation loop
+    (the first call also allocates and clears the adjoint's working set; its time is returned
+    too). Returns (ms, N, launches, ms_first, plan)."""
     L, nf = make_ctx(q, n, storage, scheme, "tg", torch, lbm)
     L.record_checkpoints(K)  # the forward run keeps the checkpoints the adjoint starts from
     L.step(steps)
     g = torch.randn(3, L.N, device="cuda", dtype=torch.float64 if storage == "fp64" else torch.float32)
-    torch.cuda.synchronize()
-    l0 = L.launches
-    t = time.perf_counter()
-    L.adjoint(g, steps, K)
-    torch.cuda.synchronize()
-    ms = (time.perf_counter() - t) * 1e3
-    launches = L.launches - l0
+    times = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        l0 = L.launches
+        t = time.perf_counter()
+        L.adjoint(g, steps, K)
+        torch.cuda.synchronize()
+        times.append((time.perf_counter() - t) * 1e3)
+        launches = L.launches - l0
+    k2, prefetched = L.adjoint_info()
     N = L.N
     L.close()
-    return ms, N, launches
+    return times[1], N, launches, times[0], {"sub_segment": k2, "host_checkpoints_prefetched": prefetched}
 
 
 def time_e2e(q, n, storage, steps, torch, lbm):
@@ -353,13 +359,16 @@ def run_sweep(args, torch, lbm):
                                          (host_mem_available() / 1e9, 1.2 * need_host / 1e9)}), flush=True)
             continue
         try:
-            ms, N, launches = time_adjoint(q, n, st, sc, steps, K, torch, lbm)
+            ms, N, launches, ms1, plan = time_adjoint(q, n, st, sc, steps, K, torch, lbm)
         except Exception as e:
             print(json.dumps({"adjoint": True, "n": n, "error": str(e)[:300]}), flush=True)
             continue
+        bpc = 2 * q * 4 + 3 * q * ELEM[st]  # adjoint kernel (lambda r+w, f_t r) + one recompute step
+        mlups = N * steps / (ms * 1e-3) / 1e6
         print(json.dumps({"adjoint": True, "lattice": f"D3Q{q}", "n": n, "storage": st, "scheme": sc, "steps": steps,
-                          "checkpoint_every": K, "mlups": N * steps / (ms * 1e-3) / 1e6, "ms": ms,
-                          "launches": launches}), flush=True)
+                          "checkpoint_every": K, "mlups": mlups, "ms": ms, "bytes_per_cell": bpc,
+                          "frac": mlups * 1e6 * bpc / 1e9 / peak, "mlups_first_call": N * steps / (ms1 * 1e-3) / 1e6,
+                          "ms_first_call": ms1, "launches": launches, **plan}), flush=True)
         torch.cuda.empty_cache()
 
 
@@ -455,9 +464,11 @@ def main():
         if rank == 0:
             r16 = variant(19, 256, "fp16s", "pull", "tg", max(10, args.steps // 2), args.warmup, torch, lbm, peak)
             sub["fwd_fp16s_256"] = {k: r16[k] for k in ("mlups_all", "kernel_gbs", "frac", "kernel_ms")}
-            msa, Na, la = time_adjoint(19, 128, "fp32", "pull", 200, 20, torch, lbm)
+            msa, Na, la, msa1, _ = time_adjoint(19, 128, "fp32", "pull", 200, 20, torch, lbm)
             sub["adjoint_fp32_128"] = {"mlups": Na * 200 / (msa * 1e-3) / 1e6, "steps": 200, "checkpoint_every": 20,
-                                       "launches": la, "note": "wall time of lbm_adjoint incl. forward recompute"}
+                                       "launches": la, "mlups_first_call": Na * 200 / (msa1 * 1e-3) / 1e6,
+                                       "note": "wall time of lbm_adjoint incl. forward recompute (second call "
+                                               "on the same forward run; the first also allocates its buffers)"}
         msE, h2d, d2h = time_e2e(q, n, storage, args.steps, torch, lbm)
         e2e = {"value": N * args.steps * world / (msE * 1e-3) / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,

@@ -20,7 +20,7 @@ namespace lbm {
 
 Shape shape_for(const Geom& g) {
     Shape s;
-    const int bx = std::min(256, ((g.nx + 31) / 32) * 32);
+    const int bx = block_x_for(g.nx);
     const int by = std::max(1, 256 / bx);
     s.block = dim3(bx, by, 1);
     s.grid = dim3((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
@@ -131,6 +131,8 @@ struct lbm_ctx {
     double* gpart = nullptr;
     bool grads_ready = false;
     int last_adj_K2 = 0;  // sub-segment length of the last adjoint (== K when flat)
+    int last_adj_prefetch = 0;       // host checkpoints the last adjoint restored ahead of use
+    std::vector<void*> adj_bufs;     // segment state buffers, kept for later adjoint calls
     double grad_theta[6] = {0};
     double grad_tau = 0.0;
 
@@ -376,8 +378,10 @@ void* ckpt_slot(lbm_ctx* c, size_t k, bool* host) {
     bool dev_ok = cudaMemGetInfo(&fr, &tot) == cudaSuccess;
     if (!dev_ok) (void)cudaGetLastError();
     const size_t LB = (size_t)c->q * c->N * c->felem;
-    const size_t reserve = (c->lam[0] ? 0 : 2 * LB + (size_t)c->d * c->N * c->felem) +
-                           (size_t)(2 * (int)std::ceil(std::sqrt((double)c->rec_K)) + 1) * SB + ((size_t)2 << 30);
+    const long long plan = 2 * (long long)std::ceil(std::sqrt((double)c->rec_K)) + 1;  // states
+    const long long to_get = std::max<long long>(0, plan - (long long)c->adj_bufs.size());
+    const size_t reserve = (c->lam[0] ? 0 : 2 * LB + (size_t)c->d * c->N * c->felem) + (size_t)to_get * SB +
+                           ((size_t)2 << 30);
     dev_ok = dev_ok && fr >= reserve + SB;
     if (c->opt.adjoint_mem_limit)  // the limit covers checkpoints and the smallest segment plan
         dev_ok = dev_ok && used + SB + (size_t)(2 * (int)std::ceil(std::sqrt((double)c->rec_K)) + 1) * SB <=
@@ -495,6 +499,7 @@ void lbm_destroy(lbm_ctx* c) {
     dev_free(c, c->lam[1], LB);
     dev_free(c, c->du0, (size_t)c->d * c->N * c->felem);
     dev_free(c, c->gpart, (size_t)c->shape.nblocks * 8 * sizeof(double));
+    for (void* p : c->adj_bufs) dev_free(c, p, SB);
     dev_free(c, c->ade_u, (size_t)c->d * c->N * c->felem);
     if (c->hout) cudaFreeHost(c->hout);
     if (c->hflag) cudaFreeHost(c->hflag);
@@ -788,9 +793,11 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
     // Memory plan for the states of one segment. Flat: the segment start plus its K-1 states.
     // Two-level: sub-checkpoints every K2 steps of the segment plus the K2-1 states of one
     // sub-segment, i.e. ceil(K/K2) + K2 - 1 buffers, at the price of a second recompute.
+    // Segment buffers are kept in the context for later calls, so they count as available.
     size_t fr = 0, tot = 0;
     LBM_CUDA(c, cudaMemGetInfo(&fr, &tot));
-    size_t avail = fr > ((size_t)1 << 30) ? fr - ((size_t)1 << 30) : 0;
+    const long long held = (long long)c->adj_bufs.size();
+    size_t avail = (fr > ((size_t)1 << 30) ? fr - ((size_t)1 << 30) : 0) + (size_t)held * SB;
     if (c->opt.adjoint_mem_limit) avail = std::min(avail, c->opt.adjoint_mem_limit);
     const long long mbuf = (long long)(avail / SB);
     auto need = [&](int k2) -> long long { return k2 >= K ? K : (K + k2 - 1) / k2 + k2 - 1; };
@@ -809,19 +816,26 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
     const int S2 = (K + K2 - 1) / K2;
     const int nbuf = (int)std::max<long long>(2, need(K2));
 
-    std::vector<void*> bufs(nbuf, nullptr), ckpt(C, nullptr);
+    std::vector<void*> ckpt(C, nullptr);
     std::vector<bool> ckpt_host(C, false);
     std::vector<void*> own;  // checkpoints this call allocated
     std::vector<bool> own_host;
+    cudaStream_t cs = nullptr;  // copy stream of the checkpoint prefetch
+    cudaEvent_t ev_free = nullptr, ev_done[2] = {nullptr, nullptr};
     auto release = [&]() {
         cudaStreamSynchronize(c->stream);
+        if (cs) {
+            cudaStreamSynchronize(cs);
+            cudaStreamDestroy(cs);
+        }
+        for (cudaEvent_t e : {ev_free, ev_done[0], ev_done[1]})
+            if (e) cudaEventDestroy(e);
         for (size_t k = 0; k < own.size(); ++k) {
             if (own_host[k])
                 cudaFreeHost(own[k]);
             else
                 dev_free(c, own[k], SB);
         }
-        for (void* p : bufs) dev_free(c, p, SB);
     };
     int rc = LBM_OK;
 #define LBM_ADJ_CHECK(expr, what)          \
@@ -833,14 +847,14 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
             return rc;                     \
         }                                  \
     } while (0)
-    for (int k = 0; k < nbuf; ++k) {
-        if (!(bufs[k] = dev_alloc(c, SB))) {
-            release();
-            return fail(c, LBM_ERR_OOM, "adjoint: segment state %d of %d (%zu bytes)", k, nbuf, SB);
-        }
+    for (long long k = held; k < nbuf; ++k) {
+        void* p = dev_alloc(c, SB);
+        if (!p) return fail(c, LBM_ERR_OOM, "adjoint: segment state %lld of %d (%zu bytes)", k, nbuf, SB);
+        c->adj_bufs.push_back(p);
         // solid-cell slots that no kernel writes stay defined
-        LBM_ADJ_CHECK(cudaMemsetAsync(bufs[k], 0, SB, c->stream), "clear");
+        LBM_CUDA(c, cudaMemsetAsync(p, 0, SB, c->stream));
     }
+    void** bufs = c->adj_bufs.data();
     const void* cf = c->coef();
     auto step_oop = [&](const void* src, void* dst, long long t) -> cudaError_t {
         c->launches += 1;
@@ -892,11 +906,57 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
         }
     }
 
+    // Host checkpoints are restored into bufs[0] (segments with even index) and one extra buffer
+    // (odd index); with that buffer, the restore of segment s-1 runs on a copy stream while
+    // segment s is recomputed and swept. Without room for it, restores are synchronous.
+    void* rbuf[2] = {bufs[0], nullptr};
+    int n_host = 0, n_dev = 0;
+    for (int k = 0; k < C; ++k) (ckpt_host[k] ? n_host : n_dev) += 1;
+    // the extra state must fit next to the device checkpoints and the segment plan
+    bool room1 = (long long)c->adj_bufs.size() > nbuf;
+    if (!room1) {
+        LBM_ADJ_CHECK(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
+        room1 = fr > SB + ((size_t)1 << 30);
+    }
+    if (c->opt.adjoint_mem_limit) room1 = room1 && (size_t)(n_dev + nbuf + 1) * SB <= c->opt.adjoint_mem_limit;
+    if (n_host > 1 && room1) {
+        if ((long long)c->adj_bufs.size() <= nbuf) {
+            void* p = dev_alloc(c, SB);
+            if (p) {
+                c->adj_bufs.push_back(p);
+                bufs = c->adj_bufs.data();
+                rbuf[0] = bufs[0];
+                LBM_ADJ_CHECK(cudaMemsetAsync(p, 0, SB, c->stream), "clear");
+            }
+        }
+        if ((long long)c->adj_bufs.size() > nbuf) {
+            rbuf[1] = bufs[nbuf];
+            LBM_ADJ_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "copy stream");
+            LBM_ADJ_CHECK(cudaEventCreateWithFlags(&ev_free, cudaEventDisableTiming), "event");
+            LBM_ADJ_CHECK(cudaEventCreateWithFlags(&ev_done[0], cudaEventDisableTiming), "event");
+            LBM_ADJ_CHECK(cudaEventCreateWithFlags(&ev_done[1], cudaEventDisableTiming), "event");
+        }
+    }
+    std::vector<bool> issued(C, false);
+    int prefetched = 0;
+    // Restore of host checkpoint s on the copy stream, after all work enqueued so far on the
+    // context's stream (the previous user of its buffer is the segment two places later).
+    auto prefetch = [&](int s) -> cudaError_t {
+        cudaError_t e = cudaEventRecord(ev_free, c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_free, 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rbuf[s & 1], ckpt[s], SB, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_done[s & 1], cs);
+        issued[s] = true;
+        ++prefetched;
+        return e;
+    };
+
     // Seed from f(n), the context's current state.
     int lc = 0;
     LBM_ADJ_CHECK(c->ops->adj_seed(c->geom, cf, layout_now(c, n), state_ptr(c), loss_grad, c->lam[lc], c->stream),
                   "adjoint seed");
     c->launches += 1;
+    if (cs && ckpt_host[C - 1]) LBM_ADJ_CHECK(prefetch(C - 1), "checkpoint prefetch");
     // adjoint steps t1+len-1 .. t1 over states held in st[0..len-1]
     auto sweep = [&](const std::vector<const void*>& st, long long t1) -> cudaError_t {
         for (int j = (int)st.size() - 1; j >= 0; --j) {
@@ -914,10 +974,16 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
         const int len = (int)std::min<long long>(K, n - t0);
         const void* start = ckpt[s];
         if (ckpt_host[s]) {
-            LBM_ADJ_CHECK(cudaMemcpyAsync(bufs[0], ckpt[s], SB, cudaMemcpyHostToDevice, c->stream),
-                          "checkpoint restore");
-            start = bufs[0];
+            if (issued[s]) {
+                LBM_ADJ_CHECK(cudaStreamWaitEvent(c->stream, ev_done[s & 1], 0), "checkpoint wait");
+                start = rbuf[s & 1];
+            } else {
+                LBM_ADJ_CHECK(cudaMemcpyAsync(bufs[0], ckpt[s], SB, cudaMemcpyHostToDevice, c->stream),
+                              "checkpoint restore");
+                start = bufs[0];
+            }
         }
+        if (cs && s > 0 && ckpt_host[s - 1]) LBM_ADJ_CHECK(prefetch(s - 1), "checkpoint prefetch");
         if (K2 >= K) {  // flat: states t0 + j in bufs[j], j = 1 .. len-1
             std::vector<const void*> st(len);
             st[0] = start;
@@ -929,7 +995,7 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
         } else {  // two-level: sub-checkpoints in bufs[1 .. S2-1], sub-segment states after them
             std::vector<const void*> sub(S2);
             sub[0] = start;
-            void** subseg = bufs.data() + S2;
+            void** subseg = bufs + S2;
             const int nsub = (len + K2 - 1) / K2;
             for (int j = 1; j < nsub; ++j) {
                 const void* cur = sub[j - 1];
@@ -973,7 +1039,27 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
     c->grad_tau = c->hout[6];
     c->grads_ready = true;
     c->last_adj_K2 = K2;
+    c->last_adj_prefetch = prefetched;
     release();
+    return LBM_OK;
+}
+
+int lbm_adjoint_info(const lbm_ctx* c, int* sub_segment, int* prefetched) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (sub_segment) *sub_segment = c->last_adj_K2;
+    if (prefetched) *prefetched = c->last_adj_prefetch;
+    return LBM_OK;
+}
+
+int lbm_adjoint_release(lbm_ctx* c) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    const size_t SB = c->state_bytes(), LB = (size_t)c->q * c->N * c->felem;
+    for (void* p : c->adj_bufs) dev_free(c, p, SB);
+    c->adj_bufs.clear();
+    dev_free(c, c->lam[0], LB);
+    dev_free(c, c->lam[1], LB);
+    c->lam[0] = c->lam[1] = nullptr;
     return LBM_OK;
 }
 

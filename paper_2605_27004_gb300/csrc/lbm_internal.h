@@ -43,6 +43,21 @@ struct Shape {
 };
 Shape shape_for(const Geom& g);
 
+// Block width for n threads along x: a multiple of 32 up to 256 that wastes the fewest threads
+// in the last block of a row (wider on ties), so that e.g. 384 threads per row run as two
+// 192-thread blocks instead of two 256-thread blocks a quarter of which idle.
+inline int block_x_for(int n) {
+    int best = 32, waste = 1 << 30;
+    for (int bx = 256; bx >= 32; bx -= 32) {
+        const int w = ((n + bx - 1) / bx) * bx - n;
+        if (w < waste) {
+            waste = w;
+            best = bx;
+        }
+    }
+    return best;
+}
+
 // Kernel launchers of one (lattice, storage) pair. `coef` points at a Coef<double> (storage
 // LBM_FP64) or a Coef<float> (every other storage). Field pointers (rho, u, Pi, f, grad, lam,
 // du0) are double for FP64 and float otherwise; population pointers have the storage type.

@@ -373,8 +373,8 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3)
 inline Shape shape_pairs(const Geom& g) {
     Shape s;
     const int np = g.nx / 2;
-    const int bx = np >= 256 ? 256 : ((np + 31) / 32) * 32;
-    const int by = 256 / bx;
+    const int bx = block_x_for(np);
+    const int by = std::max(1, 256 / bx);
     s.block = dim3(bx, by, 1);
     s.grid = dim3((np + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
     s.nblocks = (long long)s.grid.x * s.grid.y * s.grid.z;

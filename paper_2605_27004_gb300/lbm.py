@@ -55,6 +55,8 @@ SIGNATURES = {
     "lbm_populations": (_I, [_P, _P]),
     "lbm_totals": (_I, [_P, _P, _P]),
     "lbm_adjoint": (_I, [_P, _P, _I, _I]),
+    "lbm_adjoint_release": (_I, [_P]),
+    "lbm_adjoint_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "lbm_record_checkpoints": (_I, [_P, _I]),
     "lbm_gradients": (_I, [_P, _P, _P, _P]),
     "lbm_state_bytes": (_I, [_P, ctypes.POINTER(_S)]),
@@ -278,6 +280,15 @@ class LBM:
         g = self._field(loss_grad, (self.d, self.N))
         _check(load().lbm_adjoint(self.ctx, _ptr(g), int(n), int(checkpoint_every)), self.ctx)
 
+    def adjoint_info(self):
+        """(sub-segment length, host checkpoints prefetched) of the last adjoint."""
+        k2, pf = ctypes.c_int(), ctypes.c_int()
+        _check(load().lbm_adjoint_info(self.ctx, ctypes.byref(k2), ctypes.byref(pf)), self.ctx)
+        return k2.value, pf.value
+
+    def adjoint_release(self):
+        _check(load().lbm_adjoint_release(self.ctx), self.ctx)
+
     def gradients(self, du0=True):
         dth = np.zeros(3 if self.d == 2 else 6)
         dtau = ctypes.c_double()
@@ -402,6 +413,10 @@ def lbm_totals(ctx: LBM):
 
 def lbm_adjoint(ctx: LBM, loss_grad, n, checkpoint_every=0):
     ctx.adjoint(loss_grad, n, checkpoint_every)
+
+
+def lbm_adjoint_release(ctx: LBM):
+    ctx.adjoint_release()
 
 
 def lbm_gradients(ctx: LBM):

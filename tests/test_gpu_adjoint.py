@@ -93,18 +93,32 @@ def test_recorded_and_host_checkpoints_give_identical_gradients(scheme):
     Th = rand_theta(91, 3, 0.03)
     rho0, u0 = inputs.noise_field(N, 3, 0.04, 92, rho_amp=0.01)
     g = torch.as_tensor(np.random.default_rng(93).standard_normal((3, N)), dtype=torch.float32)
+    SB = 19 * N * 4
     out = []
-    for mode in ("recorded", "own", "host"):
-        # host: the limit leaves room for the K segment states and at most one checkpoint
-        L = lbm.LBM(q, *dims, 0.7, Th, storage="fp32", scheme=scheme,
-                    adjoint_mem_limit=(K + 1) * 19 * N * 4 if mode == "host" else 0)
-        if mode == "recorded":
+    for mode in ("recorded", "own", "host", "recorded_host"):
+        # host: the limit leaves room for the K segment states and at most one checkpoint, so the
+        # restores are synchronous; recorded_host: recording keeps one checkpoint on the device
+        # (it reserves 2 ceil(sqrt K) + 1 = 7 states), the other four go to host memory, and the
+        # flat plan (5 states) leaves one state for restoring them one segment ahead of use
+        limit = {"host": (K + 1) * SB, "recorded_host": 8 * SB}.get(mode, 0)
+        L = lbm.LBM(q, *dims, 0.7, Th, storage="fp32", scheme=scheme, adjoint_mem_limit=limit)
+        if mode.startswith("recorded"):
             L.record_checkpoints(K)
         L.init(torch.as_tensor(rho0), torch.as_tensor(u0))
         L.step(steps)
         L.adjoint(g, steps, K)
+        k2, prefetched = L.adjoint_info()
+        assert k2 == K
+        assert prefetched == (4 if mode == "recorded_host" else 0), mode
         dth, dtau, du0 = L.gradients()
         out.append((dth, dtau, du0.cpu()))
+        # a second call reuses the kept working set; a call after releasing it allocates anew
+        L.adjoint(g, steps, K)
+        out.append(tuple(x.cpu() if hasattr(x, "cpu") else x for x in L.gradients()))
+        L.adjoint_release()
+        L.adjoint(g, steps, K)
+        out.append(tuple(x.cpu() if hasattr(x, "cpu") else x for x in L.gradients()))
+        L.close()
     for dth, dtau, du0 in out[1:]:
         assert np.array_equal(dth, out[0][0]) and dtau == out[0][1] and torch.equal(du0, out[0][2])
 
@@ -132,6 +146,7 @@ def test_two_level_segments_match_flat(scheme, recorded):
         L.init(torch.as_tensor(rho0), torch.as_tensor(u0))
         L.step(steps)
         L.adjoint(g, steps, K)
+        assert (L.adjoint_info()[0] < K) == (limit > 0)
         dth, dtau, du0 = L.gradients()
         out.append((dth, dtau, du0.cpu()))
     assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1] and torch.equal(out[0][2], out[1][2])
