@@ -122,10 +122,11 @@ struct Cell {
     uint32_t R[3][3];
 };
 
-__device__ __forceinline__ void make_cell_at(const Geom& g, int x, int y, int z, Cell& c) {
-    c.x = x;
-    c.y = y;
-    c.z = z;
+__device__ __forceinline__ bool make_cell(const Geom& g, Cell& c) {
+    c.x = blockIdx.x * blockDim.x + threadIdx.x;
+    c.y = blockIdx.y * blockDim.y + threadIdx.y;
+    c.z = blockIdx.z;
+    if (c.x >= g.nx || c.y >= g.ny) return false;
     const uint32_t yy[3] = {(uint32_t)(c.y + 1 == g.ny ? 0 : c.y + 1), (uint32_t)c.y,
                             (uint32_t)(c.y == 0 ? g.ny - 1 : c.y - 1)};
     const uint32_t zz[3] = {(uint32_t)(c.z + 1 == g.nz ? 0 : c.z + 1), (uint32_t)c.z,
@@ -139,13 +140,6 @@ __device__ __forceinline__ void make_cell_at(const Geom& g, int x, int y, int z,
 #pragma unroll
         for (int b = 0; b < 3; ++b) c.R[a][b] = nx * (yy[a] + ny * zz[b]);
     c.n = c.X[1] + c.R[1][1];
-}
-
-__device__ __forceinline__ bool make_cell(const Geom& g, Cell& c) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= g.nx || y >= g.ny) return false;
-    make_cell_at(g, x, y, blockIdx.z, c);
     return true;
 }
 
@@ -406,56 +400,6 @@ __global__ void __launch_bounds__(256) k_step_aa(Geom g, Coef<typename Store<S>:
     const Macro<T> m = bgk<Q, T, Store<S>::fix_momentum, Store<S>::fold_omega>(cf, d);
     if (bad_cell(m)) *flag = 1;
     aa_store<Q, S, MASK, ODD>(c, lw, cf, dst, d);
-}
-
-// ---------------------------------------------------------------------------------------------
-// Stream + collide with walls, marching along z. In a box with walls every gathered address
-// depends on the cell's link word, so a one-cell-per-thread kernel waits for two memory round
-// trips per cell (link word, then populations). Here a thread updates the cells (x, y, z0 ..
-// z0 + ZB - 1) in turn and loads the link word of the next cell before gathering the current
-// one, so that each cell costs one round trip. ODD < 0: pull step (k_step_pull); ODD = 0 / 1:
-// even / odd AA step (k_step_aa), in place. Solid cells are skipped.
-// ---------------------------------------------------------------------------------------------
-template <int Q, int S, int ODD, int ZB>
-__global__ void __launch_bounds__(256, 4) k_step_walls(Geom g, Coef<typename Store<S>::T> cf,
-                                                       const Planes<const typename Store<S>::type> src,
-                                                       const Planes<typename Store<S>::type> dst,
-                                                       int* __restrict__ flag) {
-    using T = typename Store<S>::T;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= g.nx || y >= g.ny) return;
-    const int z0 = blockIdx.z * ZB;
-    const int z1 = min(z0 + ZB, g.nz);
-    const uint32_t plane = (uint32_t)g.nx * (uint32_t)g.ny;
-    const uint32_t* lp = g.link + ((uint32_t)x + (uint32_t)g.nx * (uint32_t)y + plane * (uint32_t)z0);
-    uint32_t next = __ldg(lp);
-    bool bad = false;
-#pragma unroll 1
-    for (int z = z0; z < z1; ++z) {
-        const uint32_t lw = next;
-        lp += plane;
-        if (z + 1 < z1) next = __ldg(lp);
-        if (lw & LINK_SOLID) continue;
-        Cell c;
-        make_cell_at(g, x, y, z, c);
-        T d[Q];
-        if (ODD < 0)
-            gather<Q, S, true, LAYOUT_PULL, true>(c, lw, cf, src, d);
-        else if (ODD)
-            gather<Q, S, true, LAYOUT_AAODD, false>(c, lw, cf, src, d);
-        else
-            gather<Q, S, true, LAYOUT_LOCAL, false>(c, lw, cf, src, d);
-        const Macro<T> m = bgk<Q, T, Store<S>::fix_momentum, Store<S>::fold_omega>(cf, d);
-        bad = bad || bad_cell(m);
-        if (ODD < 0) {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) st_raw(dst.p[i] + c.n, from_shifted<S>(d[i], cf.r[i]));
-        } else {
-            aa_store<Q, S, true, (ODD > 0 ? 1 : 0)>(c, lw, cf, dst, d);
-        }
-    }
-    if (bad) *flag = 1;
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -8,12 +8,6 @@
 namespace lbm {
 
 // ---------------------------------------------------------------------------------------------
-// Cells per thread along z in the wall kernels (k_step_walls).
-constexpr int WALL_ZB = 8;
-inline dim3 walls_grid(const Shape& sh, const Geom& g) {
-    return dim3(sh.grid.x, sh.grid.y, (unsigned)((g.nz + WALL_ZB - 1) / WALL_ZB));
-}
-
 template <int Q, int S>
 struct Launch {
     using ST = typename Store<S>::type;
@@ -66,7 +60,7 @@ struct Launch {
             }
         }
         if (g.link)
-            k_step_walls<Q, S, -1, WALL_ZB><<<walls_grid(sh, g), sh.block, 0, st>>>(g, cf, a, b, flag);
+            k_step_pull<Q, S, true><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
         else
             k_step_pull<Q, S, false><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
         return cudaGetLastError();
@@ -90,9 +84,9 @@ struct Launch {
         }
         if (g.link) {
             if (odd)
-                k_step_walls<Q, S, 1, WALL_ZB><<<walls_grid(sh, g), sh.block, 0, st>>>(g, cf, a, b, flag);
+                k_step_aa<Q, S, true, 1><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
             else
-                k_step_walls<Q, S, 0, WALL_ZB><<<walls_grid(sh, g), sh.block, 0, st>>>(g, cf, a, b, flag);
+                k_step_aa<Q, S, true, 0><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
         } else {
             if (odd)
                 k_step_aa<Q, S, false, 1><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
