@@ -716,8 +716,12 @@ __global__ void __launch_bounds__(256) k_adj_seed(Geom g, Coef<typename Store<S>
     for (int i = 0; i < Q; ++i) lam.p[i][c.n] = (vdot<T>(vel<Q>(i), gx, gy, gz) - gu) * inv;
 }
 
+// Register caps: D2Q9/D3Q19 at most 64 (four 256-thread blocks per SM instead of three; the few
+// spilled values stay in L1): FP16 AA adjoint at 256^3 0.69 -> 0.77 of the copy peak, FP32 pull
+// 0.87 -> 0.90 (measured). D3Q27 at most 128 (two blocks instead of one at 189 registers, no
+// spills). FP64 storage is left uncapped.
 template <int Q, int S, bool MASK, int LAYOUT>
-__global__ void __launch_bounds__(256) k_adj_step(Geom g, Coef<typename Store<S>::T> cf,
+__global__ void __launch_bounds__(256, S == 1 ? 1 : Q == 27 ? 2 : 4) k_adj_step(Geom g, Coef<typename Store<S>::T> cf,
                                                   const Planes<const typename Store<S>::type> src,
                                                   const Planes<const typename Store<S>::T> lam_next,
                                                   const Planes<typename Store<S>::T> lam, double* __restrict__ gpart) {
