@@ -295,6 +295,20 @@ def cpu_baseline(budget_s=12.0):
             "sample": f"D3Q19 Taylor-Green on a 64^3 box, {steps} steps of the FP64 push oracle"}
 
 
+def job_throughput(ms_local, cells, steps, dist, torch, device="cuda"):
+    """Whole-job throughput of independent replicas (one per rank): the slowest rank's time (MAX
+    over ranks) and the cells all ranks updated, cells x steps x world size, per second in MLUPS.
+    Returns (ms, mlups)."""
+    world = 1
+    ms = float(ms_local)
+    if dist is not None:
+        world = dist.get_world_size()
+        t = torch.tensor([ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, cells * steps * world / (ms * 1e-3) / 1e6
+
+
 # ------------------------------------------------------------------------------------------------
 def run_reference(args):
     """Reference arm: the oracle, as it stands, timed on the host cores (rank 0 only)."""
@@ -448,11 +462,7 @@ def main():
     barrier()
     L.close()
     del L
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    mlups = N * args.steps * world / (ms * 1e-3) / 1e6
+    ms, mlups = job_throughput(ms, N, args.steps, dist, torch, device="cuda")
     bpc = 2 * q * ELEM[storage]
     achieved = bpc * N / (kms * 1e-3) / 1e9
     rec = NCU_TRAFFIC.get("d3q19_fp32_pull")
