@@ -120,4 +120,4 @@ def test_full_size_fp32_against_fp64_5000_steps():
         for t, (a, b) in enumerate(zip(runs[storage], runs["fp64"])):
             err = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
             print(f"{storage} after {(1000, 5000)[t]} steps: relative u L2 {err:.3e}")
-            assert err < (1e-5, 1e-4)[t]
+            assert err < 1e-5  # measured 1.5e-6 / 5.0e-6 (FP32), 9.4e-7 / 4.3e-6 (shifted FP32)
