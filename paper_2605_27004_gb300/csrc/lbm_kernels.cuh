@@ -332,31 +332,6 @@ __device__ __forceinline__ bool bad_cell(const Macro<T>& m) {
     return !(m.rho > T(0)) || !isfinite(m.ux + m.uy + m.uz);
 }
 
-// A solid cell's slots are never read (a gather that meets a solid neighbour takes the own
-// cell's opposite slot instead) and never written by another cell. A solid cell that shares a
-// 32-byte DRAM sector of its planes with a fluid cell of its warp nevertheless writes zeros to its
-// slots, so that every sector the fluid cells write is written whole: a partly written sector
-// would be read from DRAM and merged before it is written back. Used by the pull step, whose
-// destination sectors are not in L2; the in-place AA steps write sectors their warp has just
-// read, so they gain nothing (measured: FP32 0.52 -> 0.50, FP16 0.41 -> 0.17). Blocks are a multiple of 32
-// threads wide, so the lanes of a warp are consecutive cells of one row. Returns true for a
-// solid cell (which then does nothing else).
-template <int Q, int S>
-__device__ __forceinline__ bool solid_fill(uint32_t lw, uint32_t n, const Planes<typename Store<S>::type>& dst) {
-    using ST = typename Store<S>::type;
-    const bool solid = (lw & LINK_SOLID) != 0u;
-    const unsigned fluid_lanes = __ballot_sync(__activemask(), !solid);
-    if (!solid) return false;
-    constexpr int G = 32 / (int)sizeof(ST);  // cells per sector: 4, 8 or 16
-    const int lane = threadIdx.x & 31;
-    const unsigned group = ((1u << G) - 1u) << (lane & ~(G - 1));
-    if (fluid_lanes & group) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) dst.p[i][n] = ST(0);
-    }
-    return true;
-}
-
 // ---------------------------------------------------------------------------------------------
 // Fused stream + collide, two arrays, pull form: gather f(t) from the post-collision array of
 // the previous step, relax, store at the own cell. One launch per time step.
@@ -369,15 +344,24 @@ __global__ void __launch_bounds__(256) k_step_pull(Geom g, Coef<typename Store<S
     Cell c;
     if (!make_cell(g, c)) return;
     const uint32_t lw = link_of<MASK>(g, c);
-    // FP32/FP64 only: measured on the 512^3 porous D3Q27 case, 0.545 -> 0.62 of the copy peak for
-    // FP32; the issue-bound FP16 kernel loses (0.39 -> 0.36) to the extra store instructions
-    if (MASK && (S != 3 ? solid_fill<Q, S>(lw, c.n, dst) : (lw & LINK_SOLID) != 0u)) return;
+    // With walls, a warp that holds a fluid cell stores all its lanes: a solid cell's slots are
+    // never read (a gather that meets a solid neighbour takes the own cell's opposite slot) nor
+    // written by another cell, so its lanes store zeros there, in the same store instructions as
+    // the fluid lanes. Every destination sector of the warp is then written whole; a partly
+    // written sector is read from DRAM and merged before it is written back.
+    const bool solid = MASK && (lw & LINK_SOLID);
+    if (MASK && __all_sync(__activemask(), solid)) return;
     T d[Q];
-    gather<Q, S, MASK, LAYOUT_PULL, true>(c, lw, cf, src, d);
-    const Macro<T> m = bgk<Q, T, Store<S>::fix_momentum, Store<S>::fold_omega>(cf, d);
-    if (bad_cell(m)) *flag = 1;
+    if (!solid) {
+        gather<Q, S, MASK, LAYOUT_PULL, true>(c, lw, cf, src, d);
+    } else {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st_raw(dst.p[i] + c.n, from_shifted<S>(d[i], cf.r[i]));
+        for (int i = 0; i < Q; ++i) d[i] = T(0);
+    }
+    const Macro<T> m = bgk<Q, T, Store<S>::fix_momentum, Store<S>::fold_omega>(cf, d);
+    if (!solid && bad_cell(m)) *flag = 1;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st_raw(dst.p[i] + c.n, solid ? T(0) : from_shifted<S>(d[i], cf.r[i]));
 }
 
 // ---------------------------------------------------------------------------------------------
