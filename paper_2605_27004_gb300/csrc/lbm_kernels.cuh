@@ -618,59 +618,127 @@ struct AdjAcc {
     T P[6], Qm[6];  // xx yy zz xy xz yz
 };
 
+// Component index of the symmetric pair (a, b) in the xx yy zz xy xz yz order, and of the
+// symmetric triple (a, b, c) among the third-order components xxy xxz xyy yyz xzz yzz xyz
+// (a triple with one index three times, e.g. xxx, equals the first moment on the lattice,
+// since c_a^3 = c_a for components in {-1, 0, 1}).
+__host__ __device__ constexpr int sym2(int a, int b) {
+    return a == b ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5));
+}
+__host__ __device__ constexpr int sym3_sorted(int a, int b, int c) {
+    return (a == 0 && b == 0 && c == 1) ? 0 : (a == 0 && b == 0 && c == 2) ? 1 : (a == 0 && b == 1 && c == 1) ? 2
+           : (a == 1 && b == 1 && c == 2) ? 3 : (a == 0 && b == 2 && c == 2) ? 4 : (a == 1 && b == 2 && c == 2) ? 5 : 6;
+}
+__host__ __device__ constexpr int sym3(int a, int b, int c) {
+    // lo <= mid <= hi, then the sorted triple's position in the list above
+    return sym3_sorted(a < b ? (a < c ? a : c) : (b < c ? b : c),
+                       a + b + c - (a < b ? (a < c ? a : c) : (b < c ? b : c)) - (a > b ? (a > c ? a : c) : (b > c ? b : c)),
+                       a > b ? (a > c ? a : c) : (b > c ? b : c));
+}
+
+// The per-pair sums of the adjoint through the moments of mu (even part sm = w (mu_i + mu_opp),
+// odd part dm = w (mu_i - mu_opp)): S0 = sum w mu, S2_ab = sum sm c_a c_b, D1_a = sum dm c_a,
+// D3_abc = sum dm c_a c_b c_c. Every sum the transposed Jacobian needs is a polynomial in u and
+// K~ times these (h_i = c_i.K~.c_i + h_0, h_0 = -cs2 tr K~):
+//   Q0 = u.D1,  B = 3 S0 + 2 c3 Q0,  P_ab = S2_ab,  Qm_ab = D3_abc u_c,  V = D1,
+//   v0 = (1 + 3/2 |u|^2) S0 + 9/2 (K~:S2 + h_0 S0) - 9/2 u.S2.u - 2 c3 (D3[u,u,u] - |u|^2 Q0),
+//   Va_a = 3 D1_a + 9 (S2 u)_a + c3 (3 D3[a,u,u] - |u|^2 D1_a + 3 (K~_bc D3_abc + h_0 D1_a)),
+// i.e. the direction loop only adds mu into 16 (D3Q19, D2Q9) or 17 (D3Q27) moments. The
+// tau-gradient sum gE = sum_i mu_i (feq_i - f_i) keeps its per-direction differences (each
+// difference of two close values is exact, so the non-equilibrium part keeps its precision).
 template <int Q, typename T>
 __device__ __forceinline__ AdjAcc<T> adj_accumulate(const Coef<T>& cf, const EqCell<T>& e, const T (&mu)[Q],
                                                     const T* d) {
-    AdjAcc<T> A;
-    A.v0 = A.B = A.P0 = A.Q0 = A.gE = T(0);
+    constexpr int D = Lat<Q>::D;
+    T S0 = T(weight<Q>(0)) * mu[0], S2[6], D1[3], D3[7], gE = T(0);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) A.Va[a] = A.V[a] = T(0);
+    for (int k = 0; k < 6; ++k) S2[k] = T(0);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) A.P[k] = A.Qm[k] = T(0);
-    const T usq = e.usq;
-    const T c3 = cf.c3;
-    {  // rest direction
-        const T w = T(weight<Q>(0));
-        const T m = w * mu[0];
-        A.P0 += m;
-        A.B += T(3) * m;
-        A.v0 += m * (T(1) + T(4.5) * cf.h[0] + T(1.5) * usq);
-        if (d) A.gE += mu[0] * (rest_eq<Q, T>(cf, e) - d[0]);
-    }
+    for (int a = 0; a < 3; ++a) D1[a] = T(0);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) D3[k] = T(0);
+    if (d) gE = mu[0] * (rest_eq<Q, T>(cf, e) - d[0]);
 #pragma unroll
     for (int k = 0; k < Lat<Q>::P; ++k) {
         const int i = 2 * k + 1;
         const Vec3 v = vel<Q>(i);
+        const int c[3] = {v.x, v.y, v.z};
         const T w = T(weight<Q>(i));
-        T E, O, uc;
-        pair_eq<Q, T>(cf, e, k, E, O, uc);
-        const T ms = mu[i] + mu[i + 1], md = mu[i] - mu[i + 1];
-        const T sm = w * ms;
-        const T dm = w * md;
-        const T uc2 = uc * uc;
-        // per-direction differences feq_i - f_i: the two operands are close, so each difference is
-        // exact and the small non-equilibrium part keeps its relative precision
-        if (d) A.gE += mu[i] * ((E + O) - d[i]) + mu[i + 1] * ((E - O) - d[i + 1]);
-        A.P0 += sm;
-        A.Q0 += uc * dm;
-        A.B += T(3) * sm + T(2) * c3 * uc * dm;
-        A.v0 += sm * (T(1) + T(4.5) * cf.h[i] - T(4.5) * uc2 + T(1.5) * usq) - T(2) * c3 * uc * (uc2 - usq) * dm;
-        const T al = (T(3) + c3 * (T(3) * uc2 - usq + T(3) * cf.h[i])) * dm + T(9) * uc * sm;
-        add_c<T>(v, al, A.Va[0], A.Va[1], A.Va[2]);
-        add_c<T>(v, dm, A.V[0], A.V[1], A.V[2]);
+        const T sm = w * (mu[i] + mu[i + 1]), dm = w * (mu[i] - mu[i + 1]);
+        if (d) {
+            T E, O, uc;
+            pair_eq<Q, T>(cf, e, k, E, O, uc);
+            gE += mu[i] * ((E + O) - d[i]) + mu[i + 1] * ((E - O) - d[i + 1]);
+        }
+        S0 += sm;
 #pragma unroll
-        for (int p = 0; p < 6; ++p) {
-            const int ca = comp(v, p < 3 ? p : (p == 5 ? 1 : 0));
-            const int cb = comp(v, p < 3 ? p : (p == 3 ? 1 : 2));
-            const int s = ca * cb;
-            if (s == 1) {
-                A.P[p] += sm;
-                A.Qm[p] += uc * dm;
-            } else if (s == -1) {
-                A.P[p] -= sm;
-                A.Qm[p] -= uc * dm;
+        for (int a = 0; a < 3; ++a) {
+            if (c[a] == 1) D1[a] += dm;
+            if (c[a] == -1) D1[a] -= dm;
+#pragma unroll
+            for (int b = a; b < 3; ++b) {
+                const int p2 = c[a] * c[b];
+                if (p2 == 1) S2[sym2(a, b)] += sm;
+                if (p2 == -1) S2[sym2(a, b)] -= sm;
+#pragma unroll
+                for (int cc = b; cc < 3; ++cc) {
+                    if (a == b && b == cc) continue;  // c_a^3 = c_a: part of D1
+                    const int p3 = c[a] * c[b] * c[cc];
+                    if (p3 == 1) D3[sym3(a, b, cc)] += dm;
+                    if (p3 == -1) D3[sym3(a, b, cc)] -= dm;
+                }
             }
         }
+    }
+    const T u[3] = {e.ux, e.uy, e.uz};
+    const T usq = e.usq, c3 = cf.c3, h0 = cf.h[0];
+    AdjAcc<T> A;
+    A.P0 = S0;
+    A.Q0 = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) A.Q0 += u[a] * D1[a];
+    A.B = T(3) * S0 + T(2) * c3 * A.Q0;
+    A.gE = gE;
+    T S2u[3], D3uu[3], KD3[3];
+    T uS2u = T(0), KS2 = T(0), D3uuu = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        S2u[a] = D3uu[a] = KD3[a] = T(0);
+        A.V[a] = D1[a];
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            S2u[a] += S2[sym2(a, b)] * u[b];
+            KS2 += cf.K[sym2(a, b)] * S2[sym2(a, b)];
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                D3uu[a] += ((a == b && b == c) ? D1[a] : D3[sym3(a, b, c)]) * (u[b] * u[c]);
+                KD3[a] += cf.K[sym2(b, c)] * ((a == b && b == c) ? D1[a] : D3[sym3(a, b, c)]);
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        uS2u += u[a] * S2u[a];
+        D3uuu += u[a] * D3uu[a];
+    }
+    A.v0 = (T(1) + T(1.5) * usq) * S0 + T(4.5) * (KS2 + h0 * S0) - T(4.5) * uS2u -
+           T(2) * c3 * (D3uuu - usq * A.Q0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        A.Va[a] = T(3) * D1[a] + T(9) * S2u[a] +
+                  c3 * (T(3) * D3uu[a] - usq * D1[a] + T(3) * (KD3[a] + h0 * D1[a]));
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+        A.P[p] = S2[p];
+        const int a = p < 3 ? p : (p == 5 ? 1 : 0);
+        const int b = p < 3 ? p : (p == 3 ? 1 : 2);
+        T q = T(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) q += ((a == b && b == c) ? D1[a] : D3[sym3(a, b, c)]) * u[c];
+        A.Qm[p] = q;
     }
     return A;
 }
