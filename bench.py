@@ -163,6 +163,17 @@ def problem(q, n, kind):
         r2 = (ax[None, None, :] - h) ** 2 + (ax[None, :, None] - h) ** 2 + (ax[:, None, None] - h) ** 2
         phi = 1.0 + 0.5 * torch.exp(-r2 / (2 * (n / 12) ** 2))
         return (n, n, n), 0.6, theta3(), phi.reshape(-1), u.reshape(3, -1), None
+    if kind == "ade_porous":  # scalar blob carried by u_x = 0.03 through the porous medium
+        import torch
+        solid = inputs.porous_spheres(n, n, n, seed=inputs.SEED_BASE + 3)
+        fl = torch.as_tensor(1 - solid, dtype=torch.float32, device="cuda")
+        u = torch.zeros((3, n ** 3), device="cuda", dtype=torch.float32)
+        u[0] = 0.03 * fl
+        ax = torch.arange(n, device="cuda", dtype=torch.float32)
+        h = (n - 1) / 2
+        r2 = (ax[None, None, :] - h) ** 2 + (ax[None, :, None] - h) ** 2 + (ax[:, None, None] - h) ** 2
+        phi = 1.0 + 0.5 * torch.exp(-r2 / (2 * (n / 12) ** 2)).reshape(-1) * fl
+        return (n, n, n), 0.7, np.diag([0.38, 0.33, 0.29]), phi, u, solid
     if kind == "porous":
         solid = inputs.porous_spheres(n, n, n, seed=inputs.SEED_BASE + 3)
         N = n ** 3
@@ -175,10 +186,10 @@ def problem(q, n, kind):
 def make_ctx(q, n, storage, scheme, kind, torch, lbm, **kw):
     dims, tau, Th, rho0, u0, solid = problem(q, n, kind)
     dt = torch.float64 if storage == "fp64" else torch.float32
-    if kind == "ade":
-        L = lbm.ADE(q, *dims, tau, Th, u=u0.to(dt), storage=storage, scheme=scheme, **kw)
+    if kind in ("ade", "ade_porous"):
+        L = lbm.ADE(q, *dims, tau, Th, u=u0.to(dt), solid=solid, storage=storage, scheme=scheme, **kw)
         L.init(rho0.to(dt))
-        return L, L.N
+        return L, L.N if solid is None else int((solid == 0).sum())
     L = lbm.LBM(q, *dims, tau, Th, solid=solid, storage=storage, scheme=scheme, **kw)
     L.init(None if rho0 is None else torch.as_tensor(rho0, dtype=dt), torch.as_tensor(u0, dtype=dt))
     n_fluid = L.N if solid is None else int((solid == 0).sum())
@@ -210,8 +221,9 @@ def variant(q, n, storage, scheme, kind, steps, warmup, torch, lbm, peak):
     ms, kms, launches = time_steps(L, steps, warmup, torch)
     N = L.N
     L.close()
-    bpc = 2 * q * ELEM[storage] + ((3 if q != 9 else 2) * (8 if storage == "fp64" else 4) if kind == "ade" else 0)
-    alg = nf * bpc + (4 * N if kind == "porous" else 0)  # porous: one 4-byte link word per cell
+    ade = kind in ("ade", "ade_porous")
+    bpc = 2 * q * ELEM[storage] + ((3 if q != 9 else 2) * (8 if storage == "fp64" else 4) if ade else 0)
+    alg = nf * bpc + (4 * N if kind in ("porous", "ade_porous") else 0)  # walls: one 4-byte link word per cell
     gbs = alg / (kms * 1e-3) / 1e9
     return {"lattice": f"D{3 if q != 9 else 2}Q{q}", "n": n, "storage": storage, "scheme": scheme, "kind": kind,
             "cells": N, "fluid_cells": nf, "mlups_all": N * steps / (ms * 1e-3) / 1e6,
@@ -347,7 +359,9 @@ def run_sweep(args, torch, lbm):
     cases += [(27, 512, "fp32", "pull", "porous"), (27, 512, "fp16s", "pull", "porous"),
               (27, 512, "fp16s", "aa", "porous")]
     cases += [(19, 256, "fp32", "pull", "ade"), (19, 256, "fp16s", "pull", "ade"), (19, 256, "fp16s", "aa", "ade"),
-              (27, 256, "fp32", "pull", "ade"), (19, 512, "fp32", "pull", "ade")]
+              (27, 256, "fp32", "pull", "ade"), (19, 512, "fp32", "pull", "ade"),
+              (19, 512, "fp32", "pull", "ade_porous"), (19, 512, "fp16s", "pull", "ade_porous"),
+              (27, 256, "fp32", "pull", "ade_porous")]
     if args.only:
         cases = [c for c in cases if args.only in "%s_%d_%s_%s_%s" % (c[0], c[1], c[2], c[3], c[4])]
     for c in cases:
@@ -389,7 +403,7 @@ def run_sweep(args, torch, lbm):
 def run_profile(args, torch, lbm):
     """Small case for ncu: --kernel fwd runs warmup + steps forward launches; --kernel adjoint
     runs one short adjoint (seed, recompute, adjoint steps)."""
-    kind = "porous" if args.porous else "ade" if args.ade else "tg"
+    kind = ("ade_porous" if args.ade else "porous") if args.porous else "ade" if args.ade else "tg"
     L, _ = make_ctx(args.lattice, args.n, args.storage, args.scheme, kind, torch, lbm, use_graphs=-1)
     if args.kernel == "fwd":
         L.step(args.warmup + args.steps)

@@ -51,13 +51,21 @@ __global__ void __launch_bounds__(256)
     Cell c;
     if (!make_cell(g, c)) return;
     const uint32_t lw = link_of<MASK>(g, c);
-    if (MASK && (lw & LINK_SOLID)) return;
+    // with walls, solid lanes of a warp that holds a fluid cell store zeros into their own
+    // (never read) slots, so that destination sectors are written whole (as in k_step_pull)
+    const bool solid = MASK && (lw & LINK_SOLID);
+    if (MASK && __all_sync(__activemask(), solid)) return;
     T d[Q];
-    gather<Q, S, MASK, LAYOUT_PULL, true>(c, lw, cf, src, d);
-    const T s = ade_bgk<Q, T>(cf, vf, c.n, d);
-    if (!isfinite(s)) *flag = 1;
+    if (!solid) {
+        gather<Q, S, MASK, LAYOUT_PULL, true>(c, lw, cf, src, d);
+    } else {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st_raw(dst.p[i] + c.n, from_shifted<S>(d[i], cf.r[i]));
+        for (int i = 0; i < Q; ++i) d[i] = T(0);
+    }
+    const T s = ade_bgk<Q, T>(cf, vf, c.n, d);
+    if (!solid && !isfinite(s)) *flag = 1;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st_raw(dst.p[i] + c.n, solid ? T(0) : from_shifted<S>(d[i], cf.r[i]));
 }
 
 // AA pattern in place (see k_step_aa): even steps read and write the own cell, odd steps the
