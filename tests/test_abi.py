@@ -93,3 +93,10 @@ def test_scalar_calls_reject_null_context(lib):
     assert lib.lbm_ade_set_velocity(None, None, None) == -1
     assert lib.lbm_ade_velocity(None, ctypes.byref(p)) == -1
     assert not p.value
+
+
+def test_adjoint_plan_calls_reject_null_context(lib):
+    k2, pf = ctypes.c_int(7), ctypes.c_int(7)
+    assert lib.lbm_adjoint_info(None, ctypes.byref(k2), ctypes.byref(pf)) == -1
+    assert (k2.value, pf.value) == (7, 7)
+    assert lib.lbm_adjoint_release(None) == -1
