@@ -44,15 +44,20 @@ struct Shape {
 Shape shape_for(const Geom& g);
 
 // Block width for n threads along x: a multiple of 32 up to 256 that wastes the fewest threads
-// in the last block of a row (wider on ties), so that e.g. 384 threads per row run as two
-// 192-thread blocks instead of two 256-thread blocks a quarter of which idle.
+// in the last block of a row; among those, a divisor of 256 (so that blocks of bx x 256/bx
+// threads stay full: a kernel limited to two blocks per SM by its registers keeps 16 warps),
+// then the widest. 384 threads per row run as three 128 x 2 blocks instead of two 256-thread
+// blocks a quarter of which idle; 192 as 64 x 4 rather than 192 x 1.
 inline int block_x_for(int n) {
     int best = 32, waste = 1 << 30;
+    bool full = true;
     for (int bx = 256; bx >= 32; bx -= 32) {
         const int w = ((n + bx - 1) / bx) * bx - n;
-        if (w < waste) {
+        const bool f = 256 % bx == 0;
+        if (w < waste || (w == waste && f && !full)) {
             waste = w;
             best = bx;
+            full = f;
         }
     }
     return best;

@@ -73,7 +73,10 @@ struct Launch {
         const auto a = cpl(src, g);
         const auto b = mpl(dst, g);
         if constexpr (S != 1) {
-            if (pairs(g)) {  // no walls (see pairs())
+            // no walls (see pairs()); the D3Q27 odd step runs one cell per thread: its pair kernel
+            // scatters 18 x-shifted planes as single elements at 126 registers (two blocks per
+            // SM), measured 0.68 -> 0.70 (256^3) and 0.69 -> 0.71 (384^3) of the copy peak
+            if (pairs(g) && !(Q == 27 && odd)) {
                 const Shape sp = shape_pairs(g);
                 if (odd)
                     k_step_aa_odd2<Q, S><<<sp.grid, sp.block, 0, st>>>(g, cf, VelField<float>{}, a, b, flag);
