@@ -1,0 +1,88 @@
+"""The differentiation workload at its full size: D3Q19 128^3 periodic, 2000 steps,
+checkpoints every 100, initial velocity of seeded random Fourier modes (|k| <= 4, max |u| =
+0.02), target u*(2000) from a hidden SPD Theta*, loss L = mean over cells of |u(T) - u*|^2,
+evaluated at Theta = cs2 I (the start of the recovery).
+
+The gradients of the FP64 mode (dL/dTheta for the six independent entries, dL/dtau, dL/du0
+along a random direction) are checked against central finite differences of the library's own
+FP64 forward run, which does not use the adjoint kernels; the FP32-storage gradients (the
+production path, FP32 lambda with FP64 accumulation) against the FP64 ones."""
+import numpy as np
+import pytest
+
+from paper_2605_27004_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+N3, STEPS, K, TAU = 128, 2000, 100, 0.6
+CS2 = 1.0 / 3.0
+
+
+@pytest.fixture(scope="module")
+def problem():
+    import torch
+    from paper_2605_27004_gb300 import lbm
+    from paper_2605_27004_gb300.autograd import simulate, theta_matrix, theta_vector
+    seed = inputs.SEED_BASE + 4
+    th_true = theta_vector(inputs.theta_spd(seed + 10))
+    _, u0 = inputs.random_fourier_modes(N3, 4.0, 0.02, seed)
+    u0 = torch.as_tensor(u0, dtype=torch.float64, device="cuda")
+    sim = lbm.LBM(19, N3, N3, N3, TAU, theta_matrix(th_true, 3), storage="fp64")
+    with torch.no_grad():
+        target = simulate(u0, torch.as_tensor(th_true), TAU, sim, STEPS, K).clone()
+    return sim, u0, target, theta_vector(CS2 * np.eye(3))
+
+
+def _grads(sim, u0, target, th0, tau):
+    import torch
+    from paper_2605_27004_gb300.autograd import simulate
+    uu = u0.to(sim.dtype).clone().requires_grad_(True)
+    theta = torch.tensor(th0, dtype=torch.float64, requires_grad=True)
+    taut = torch.tensor(tau, dtype=torch.float64, requires_grad=True)
+    u = simulate(uu, theta, taut, sim, STEPS, K)
+    L = ((u.double() - target) ** 2).sum(0).mean()
+    L.backward()
+    return float(L.detach()), theta.grad.numpy().copy(), float(taut.grad), uu.grad.double()
+
+
+def test_fp64_gradients_match_finite_differences(problem):
+    import torch
+    from paper_2605_27004_gb300.autograd import simulate
+    sim, u0, target, th0 = problem
+    L0, gth, gtau, gu0 = _grads(sim, u0, target, th0, TAU)
+
+    def loss(th, tau, uu):
+        with torch.no_grad():
+            u = simulate(uu, torch.as_tensor(th), tau, sim, STEPS, K)
+            return float(((u - target) ** 2).sum(0).mean())
+
+    h = 1e-6
+    for k in range(6):
+        e = np.zeros(6)
+        e[k] = h
+        fd = (loss(th0 + e, TAU, u0) - loss(th0 - e, TAU, u0)) / (2 * h)
+        print(f"dL/dTheta[{k}]: adjoint {gth[k]:.9e}, finite difference {fd:.9e}")
+        assert abs(gth[k] - fd) <= 1e-5 * np.abs(gth).max()
+    fd = (loss(th0, TAU + h, u0) - loss(th0, TAU - h, u0)) / (2 * h)
+    print(f"dL/dtau: adjoint {gtau:.9e}, finite difference {fd:.9e}")
+    assert abs(gtau - fd) <= 1e-5 * abs(fd)
+    v = torch.as_tensor(np.random.default_rng(7).standard_normal(tuple(u0.shape)), device="cuda")
+    hu = 1e-4  # u0 ~ 0.02; a relative step of 5e-3 along v
+    fd = (loss(th0, TAU, u0 + hu * v) - loss(th0, TAU, u0 - hu * v)) / (2 * hu)
+    got = float((gu0 * v).sum())
+    print(f"dL/du0 . v: adjoint {got:.9e}, finite difference {fd:.9e}")
+    assert abs(got - fd) <= 1e-5 * abs(fd)
+
+
+def test_fp32_gradients_match_fp64(problem):
+    from paper_2605_27004_gb300 import lbm
+    from paper_2605_27004_gb300.autograd import theta_matrix
+    sim64, u0, target, th0 = problem
+    _, g64, t64, u64 = _grads(sim64, u0, target, th0, TAU)
+    sim32 = lbm.LBM(19, N3, N3, N3, TAU, theta_matrix(th0, 3), storage="fp32")
+    _, g32, t32, u32 = _grads(sim32, u0, target, th0, TAU)
+    eth = np.abs(g32 - g64).max() / np.abs(g64).max()
+    etau = abs(t32 - t64) / abs(t64)
+    eu = float((u32 - u64).norm() / u64.norm())
+    print(f"FP32 vs FP64: dTheta {eth:.2e}, dtau {etau:.2e}, du0 {eu:.2e}")
+    assert eth < 1e-3 and etau < 1e-2 and eu < 1e-3
