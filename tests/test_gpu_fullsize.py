@@ -94,7 +94,7 @@ def test_bench_workload_d3q19_fp32_256():
 
 
 def test_porous_d3q27_512_fp32_and_fp16():
-    """Config-3 workload at full size: D3Q27 512^3, overlapping spheres, walls at z = 0, 511,
+    """The porous workload at full size: D3Q27 512^3, overlapping spheres, walls at z = 0, 511,
     u_x = 0.03 in the fluid, tau 0.7, Theta = diag(0.38, 0.33, 0.29); FP32 and FP16-shifted."""
     import torch
     from paper_2605_27004_gb300 import lbm
@@ -113,7 +113,7 @@ def test_porous_d3q27_512_fp32_and_fp16():
 
 
 def test_aa_d3q19_768_fp16():
-    """Config-5 workload at full size: D3Q19 768^3 Taylor-Green, FP16-shifted, AA in place
+    """The largest Taylor-Green box: D3Q19 768^3 Taylor-Green, FP16-shifted, AA in place
     (samples after an odd and after an even number of steps)."""
     import torch
     from paper_2605_27004_gb300 import lbm

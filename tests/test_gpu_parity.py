@@ -66,7 +66,7 @@ def test_fp64_populations_match_oracle(q, scheme, mask, order, steps):
         assert np.all(g["rho"][solid == 1] == 0)
 
 
-def test_config1_shear_wave_fp64():
+def test_shear_wave_d2q9_64_fp64():
     """D2Q9, FP64, 64x64 periodic, tau 0.8, Theta [[0.36,0.02],[0.02,0.30]], u_x = 0.01 sin(2 pi y/64)
     + 1e-4 noise, 1000 steps: fields, totals and the shear-wave decay rate."""
     q, dims, tau = 9, (64, 64, 1), 0.8
@@ -109,7 +109,7 @@ def test_reduced_precision_taylor_green_d3q19(n, storage, tol):
 @pytest.mark.parametrize("storage,tol", [("fp32s", 1e-5), ("fp16s", 1e-3)])
 @pytest.mark.parametrize("scheme", ["pull", "aa"])
 def test_reduced_precision_porous_d3q27(storage, tol, scheme):
-    """D3Q27 porous medium between walls (config-3 recipe at 40x36x30), u_x = 0.03, 300 steps."""
+    """D3Q27 porous medium between walls (the 512^3 porous recipe at 40x36x30), u_x = 0.03, 300 steps."""
     dims = (40, 36, 30)
     solid = inputs.porous_spheres(*dims, rmin=3, rmax=6, seed=inputs.SEED_BASE + 3)
     N = int(np.prod(dims))
