@@ -3,6 +3,7 @@
 #pragma once
 #include "lbm_ade.cuh"
 #include "lbm_kernels.cuh"
+#include "lbm_adjoint2.cuh"
 #include "lbm_pairs.cuh"
 
 namespace lbm {
@@ -144,6 +145,22 @@ struct Launch {
                                 void* lam, double* gpart, cudaStream_t st) {
         const Shape sh = shape_for(g);
         const CF& cf = *static_cast<const CF*>(coef);
+        if constexpr (S == 3 && Q != 27) {  // FP16 storage without walls: two cells per thread (lbm_adjoint2.cuh;
+            // D3Q27 stays one cell per thread: at 128 registers the pair kernel would spill)
+            const Shape sp = shape_pairs(g);
+            if (!g.link && (g.nx % 2) == 0 && sp.nblocks <= sh.nblocks) {  // records fit the per-cell grid's
+                const auto a = cpl(src, g);
+                const auto ln = cfl(lam_next, g);
+                const auto l = mfl(lam, g);
+                if (layout == LAYOUT_PULL)
+                    k_adj_step2<Q, S, LAYOUT_PULL><<<sp.grid, sp.block, 0, st>>>(g, cf, a, ln, l, gpart);
+                else if (layout == LAYOUT_AAODD)
+                    k_adj_step2<Q, S, LAYOUT_AAODD><<<sp.grid, sp.block, 0, st>>>(g, cf, a, ln, l, gpart);
+                else
+                    k_adj_step2<Q, S, LAYOUT_LOCAL><<<sp.grid, sp.block, 0, st>>>(g, cf, a, ln, l, gpart);
+                return cudaGetLastError();
+            }
+        }
         LBM_BY_LAYOUT(k_adj_step, g, cf, cpl(src, g), cfl(lam_next, g), mfl(lam, g), gpart);
         return cudaGetLastError();
     }

@@ -82,6 +82,20 @@ def test_adjoint_reduced_precision(storage):
     assert abs(dtau - odtau) <= tol_tau * abs(odtau)
 
 
+@pytest.mark.parametrize("q,dims,scheme", [(19, (24, 24, 24), "aa"), (19, (30, 14, 10), "pull"),
+                                           (9, (40, 34, 1), "pull"), (9, (40, 34, 1), "aa")])
+def test_adjoint_fp16_two_cell_kernel(q, dims, scheme):
+    """FP16-shifted storage without walls and with even nx runs the two-cells-per-thread adjoint
+    kernel (all three layouts of the stored state: pull, AA even and AA odd steps): against the
+    FP64 oracle adjoint with the FP16 tolerances of test_adjoint_reduced_precision."""
+    dth, dtau, du0, odth, odtau, odu0 = _run(q, dims, None, "fp16s", scheme, 10, 40)
+    print(q, scheme, np.abs(dth - odth).max() / np.abs(odth).max(), abs(dtau - odtau) / abs(odtau),
+          rel_l2(du0, odu0))
+    assert np.abs(dth - odth).max() <= 1e-3 * np.abs(odth).max()
+    assert rel_l2(du0, odu0) < 1e-3
+    assert abs(dtau - odtau) <= 5e-2 * abs(odtau)
+
+
 @pytest.mark.parametrize("scheme", ["pull", "aa"])
 def test_recorded_and_host_checkpoints_give_identical_gradients(scheme):
     """Checkpoints recorded during the forward run, taken by the adjoint's own forward pass, or
