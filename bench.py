@@ -36,8 +36,8 @@ ELEM = {"fp32": 4, "fp32s": 4, "fp16s": 2, "fp64": 8}
 # DRAM bytes per launch from an ncu capture (profiles/), keyed by variant; used only while the
 # kernel sources hash to the recorded value (otherwise the bench reports traffic = null).
 NCU_TRAFFIC = {
-    # profiles/k_step_pull_d3q19_fp32_256.md: mean of 3 launches, 256^3, read 1.2751e+09 + write 1.2206e+09
-    "d3q19_fp32_pull": {"traffic_bytes": 2.4958e+09, "kernel_sha": "14eb06e0a2ce4643"},
+    # profiles/k_step_pull_d3q19_fp32_256.md: mean of 3 launches, 256^3, read 1.2752e+09 + write 1.2206e+09
+    "d3q19_fp32_pull": {"traffic_bytes": 2.4958e+09, "kernel_sha": "4f99d0c2fc367098"},
 }
 
 
