@@ -381,3 +381,68 @@ def test_channel_decay_between_bounce_back_walls():
     rate = -np.log(amps[1] / amps[0]) / (steps[1] - steps[0])
     ce = (tau - 0.5) * Th[2, 2] * (np.pi / H) ** 2
     assert abs(rate - ce) / ce < 0.005  # walls at cell centres would be off by 8 %
+
+
+# ------------------------------------------------------------------------------------------
+# Observables of a feq-initialised state (oracle_moments, oracle_totals): the output layout
+# ------------------------------------------------------------------------------------------
+def _distinct_theta(d):
+    """SPD Theta whose entries all differ, so a swapped component of Pi cannot go unnoticed."""
+    if d == 2:
+        return np.array([[0.36, 0.021], [0.021, 0.30]])
+    return np.array([[0.37, 0.013, -0.027], [0.013, 0.33, 0.041], [-0.027, 0.041, 0.29]])
+
+
+@pytest.mark.parametrize("q,dims", [(9, (6, 5, 1)), (19, (5, 4, 3)), (27, (4, 5, 3))])
+@pytest.mark.parametrize("walls", [False, True])
+def test_moments_of_equilibrium_state_in_documented_order(q, dims, walls):
+    """At t = 0 every fluid cell holds feq(rho0, u0), whose second moment is rho (Theta + u u)
+    (Appendix E, the second moment of the discrete equilibrium with c_s^2 A^{-1} = Theta). The
+    oracle's Pi output must give it component by component in the order xx, yy, (zz), xy, (xz,
+    yz), and rho, u must return the input fields (Eqs. a0discrete_f, a1discrete_f); solid cells
+    report zeros. The expected values come from the inputs, not from the oracle."""
+    d = oracle.D_OF_Q[q]
+    N = int(np.prod(dims))
+    rng = np.random.default_rng(7000 + q + 10 * walls)
+    Th = _distinct_theta(d)
+    rho0 = rng.uniform(0.9, 1.1, N)
+    # u components of different size so that a swapped velocity index changes the value
+    u0 = rng.uniform(-1.0, 1.0, (d, N)) * np.array([0.05, 0.03, 0.017][:d])[:, None]
+    solid = None
+    if walls:
+        solid = (rng.uniform(size=N) < 0.25).astype(np.uint8)
+    pb = oracle.Problem(q, *dims, 0.8, Th, solid=solid)
+    f = pb.init(rho0, u0)
+    rho, u, Pi = pb.moments(f)
+    fluid = np.ones(N, bool) if solid is None else solid == 0
+    pairs = [(0, 0), (1, 1), (0, 1)] if d == 2 else [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    assert Pi.shape == (len(pairs), N)
+    for k, (a, b) in enumerate(pairs):
+        want = rho0 * (Th[a, b] + u0[a] * u0[b])
+        assert np.abs(Pi[k][fluid] - want[fluid]).max() < 1e-15, (k, a, b)
+    assert np.abs(rho[fluid] - rho0[fluid]).max() < 1e-15
+    assert np.abs(u[:, fluid] - u0[:, fluid]).max() < 1e-16
+    if solid is not None:
+        assert not np.any(Pi[:, ~fluid]) and not np.any(rho[~fluid]) and not np.any(u[:, ~fluid])
+
+
+@pytest.mark.parametrize("q,dims", [(9, (6, 5, 1)), (19, (5, 4, 3)), (27, (4, 5, 3))])
+@pytest.mark.parametrize("walls", [False, True])
+def test_totals_of_equilibrium_state(q, dims, walls):
+    """Mass and momentum totals of f(0) = feq(rho0, u0) are sum rho0 and sum rho0 u0 over the
+    fluid cells (Eqs. a0discrete_f, a1discrete_f summed over the box), per component: the velocity
+    components differ in size, so a swapped momentum index fails."""
+    d = oracle.D_OF_Q[q]
+    N = int(np.prod(dims))
+    rng = np.random.default_rng(7100 + q + 10 * walls)
+    rho0 = rng.uniform(0.9, 1.1, N)
+    u0 = np.abs(rng.uniform(0.2, 1.0, (d, N))) * np.array([0.05, -0.03, 0.017][:d])[:, None]
+    solid = (rng.uniform(size=N) < 0.25).astype(np.uint8) if walls else None
+    pb = oracle.Problem(q, *dims, 0.8, _distinct_theta(d), solid=solid)
+    f = pb.init(rho0, u0)
+    mass, mom = pb.totals(f)
+    fluid = np.ones(N, bool) if solid is None else solid == 0
+    assert mom.shape == (d,)
+    assert abs(mass - rho0[fluid].sum()) < 1e-13
+    want = (rho0[None, fluid] * u0[:, fluid]).sum(axis=1)
+    assert np.abs(mom - want).max() < 1e-15 * N
