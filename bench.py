@@ -1,6 +1,7 @@
 """Benchmark: MLUPS and HBM-roofline fraction of the fused stream + collide step on one GB300.
 
-Default workload: D3Q19 anisotropic BGK, FP32 storage, 256^3 fully periodic Taylor-Green vortex
+Default workload: D3Q19 anisotropic BGK, FP32 storage (the default shifted form f - r_i, FP32
+arithmetic), 256^3 fully periodic Taylor-Green vortex
 (u0 = 0.02, rho0 = 1), tau = 0.6, Theta = R diag(0.36, 0.33, 0.30) R^T with a seeded rotation R.
 One bench step = one lattice time step over the whole box = one kernel launch. The populations
 (2 x 1.28 GB) exceed the 129 MB L2, so no flush is needed between steps.
@@ -33,11 +34,12 @@ sys.path.insert(0, ROOT)
 FALLBACK_HBM_GBS = 6800.0
 ELEM = {"fp32": 4, "fp32s": 4, "fp16s": 2, "fp64": 8}
 
-# DRAM bytes per launch from an ncu capture (profiles/), keyed by variant; used only while the
-# kernel sources hash to the recorded value (otherwise the bench reports traffic = null).
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the headline kernel from
+# one ncu capture of `python bench.py --mode profile --storage fp32s --n 256`, keyed by variant.
+# It is used only while the kernel sources hash to the value recorded with the capture; after a
+# kernel change the bench reports traffic = null (with the reason) until the capture is redone.
 NCU_TRAFFIC = {
-    # profiles/k_step_pull_d3q19_fp32_256.md: mean of 3 launches, 256^3, read 1.2752e+09 + write 1.2206e+09
-    "d3q19_fp32_pull": {"traffic_bytes": 2.4958e+09, "kernel_sha": "4f99d0c2fc367098"},
+    "d3q19_fp32s_pull": {"traffic_bytes": None, "kernel_sha": None},
 }
 
 
@@ -351,17 +353,17 @@ def run_sweep(args, torch, lbm):
     peak, src = measured_peak()
     cases = []
     for n in (64, 128, 256, 512):
-        cases += [(19, n, "fp32", "pull", "tg"), (19, n, "fp16s", "pull", "tg"), (19, n, "fp16s", "aa", "tg")]
+        cases += [(19, n, "fp32s", "pull", "tg"), (19, n, "fp16s", "pull", "tg"), (19, n, "fp16s", "aa", "tg")]
     cases += [(19, 768, "fp16s", "aa", "tg")]
-    cases += [(27, 256, "fp32", "pull", "tg"), (27, 256, "fp16s", "pull", "tg"), (27, 256, "fp16s", "aa", "tg"),
-              (19, 256, "fp32", "aa", "tg"),
-              (19, 256, "fp32s", "pull", "tg"), (9, 4096, "fp32", "pull", "tg"), (9, 64, "fp64", "pull", "tg")]
-    cases += [(27, 512, "fp32", "pull", "porous"), (27, 512, "fp16s", "pull", "porous"),
+    cases += [(27, 256, "fp32s", "pull", "tg"), (27, 256, "fp16s", "pull", "tg"), (27, 256, "fp16s", "aa", "tg"),
+              (19, 256, "fp32s", "aa", "tg"),
+              (19, 256, "fp32", "pull", "tg"), (9, 4096, "fp32s", "pull", "tg"), (9, 64, "fp64", "pull", "tg")]
+    cases += [(27, 512, "fp32s", "pull", "porous"), (27, 512, "fp16s", "pull", "porous"),
               (27, 512, "fp16s", "aa", "porous")]
-    cases += [(19, 256, "fp32", "pull", "ade"), (19, 256, "fp16s", "pull", "ade"), (19, 256, "fp16s", "aa", "ade"),
-              (27, 256, "fp32", "pull", "ade"), (19, 512, "fp32", "pull", "ade"),
-              (19, 512, "fp32", "pull", "ade_porous"), (19, 512, "fp16s", "pull", "ade_porous"),
-              (27, 256, "fp32", "pull", "ade_porous")]
+    cases += [(19, 256, "fp32s", "pull", "ade"), (19, 256, "fp16s", "pull", "ade"), (19, 256, "fp16s", "aa", "ade"),
+              (27, 256, "fp32s", "pull", "ade"), (19, 512, "fp32s", "pull", "ade"),
+              (19, 512, "fp32s", "pull", "ade_porous"), (19, 512, "fp16s", "pull", "ade_porous"),
+              (27, 256, "fp32s", "pull", "ade_porous")]
     if args.only:
         cases = [c for c in cases if args.only in "%s_%d_%s_%s_%s" % (c[0], c[1], c[2], c[3], c[4])]
     for c in cases:
@@ -374,8 +376,8 @@ def run_sweep(args, torch, lbm):
             r = {"case": c, "error": str(e)[:200]}
         print(json.dumps(r), flush=True)
         torch.cuda.empty_cache()
-    for (q, n, st, sc, K, steps) in [(19, 128, "fp32", "pull", 20, 200), (19, 128, "fp16s", "pull", 20, 200),
-                                     (19, 256, "fp32", "pull", 20, 100), (19, 256, "fp16s", "aa", 20, 100),
+    for (q, n, st, sc, K, steps) in [(19, 128, "fp32s", "pull", 20, 200), (19, 128, "fp16s", "pull", 20, 200),
+                                     (19, 256, "fp32s", "pull", 20, 100), (19, 256, "fp16s", "aa", 20, 100),
                                      (19, 512, "fp16s", "aa", 20, 200), (19, 768, "fp16s", "aa", 20, 200)]:
         if args.only and args.only not in "adj_%d_%d_%s_%s" % (q, n, st, sc):
             continue
@@ -428,7 +430,7 @@ def main():
     ap.add_argument("--only", default="", help="sweep: substring filter on case names")
     ap.add_argument("--lattice", type=int, default=19)
     ap.add_argument("--n", type=int, default=128)
-    ap.add_argument("--storage", default="fp32")
+    ap.add_argument("--storage", default="fp32s")
     ap.add_argument("--scheme", default="pull")
     ap.add_argument("--kernel", default="fwd", choices=["fwd", "adjoint"])
     ap.add_argument("--porous", action="store_true")
@@ -464,7 +466,7 @@ def main():
         torch.cuda.synchronize()
 
     peak, peak_src = measured_peak()
-    q, n, storage = 19, 256, "fp32"
+    q, n, storage = 19, 256, "fp32s"
     cpu = cpu_baseline() if (rank == 0 and world == 1 and not args.no_extras) else None
 
     # timed region: K forward steps of the 256^3 D3Q19 FP32 workload (independent replica per rank)
@@ -479,8 +481,11 @@ def main():
     ms, mlups = job_throughput(ms, N, args.steps, dist, torch, device="cuda")
     bpc = 2 * q * ELEM[storage]
     achieved = bpc * N / (kms * 1e-3) / 1e9
-    rec = NCU_TRAFFIC.get("d3q19_fp32_pull")
-    traffic = rec["traffic_bytes"] if rec and rec.get("kernel_sha") == kernel_source_hash() else None
+    rec = NCU_TRAFFIC.get("d3q19_fp32s_pull")
+    fresh = bool(rec) and rec.get("traffic_bytes") is not None and rec.get("kernel_sha") == kernel_source_hash()
+    traffic = rec["traffic_bytes"] if fresh else None
+    traffic_note = ("ncu capture of the same kernel source (sha %s)" % rec["kernel_sha"] if fresh else
+                    "null: no ncu capture of the current kernel source (sha %s)" % kernel_source_hash())
     torch.cuda.empty_cache()
 
     sub, e2e = {}, None
@@ -488,16 +493,16 @@ def main():
         if rank == 0:
             r16 = variant(19, 256, "fp16s", "pull", "tg", max(10, args.steps // 2), args.warmup, torch, lbm, peak)
             sub["fwd_fp16s_256"] = {k: r16[k] for k in ("mlups_all", "kernel_gbs", "frac", "kernel_ms")}
-            msa, Na, la, msa1, _ = time_adjoint(19, 128, "fp32", "pull", 200, 20, torch, lbm)
-            sub["adjoint_fp32_128"] = {"mlups": Na * 200 / (msa * 1e-3) / 1e6, "steps": 200, "checkpoint_every": 20,
+            msa, Na, la, msa1, _ = time_adjoint(19, 128, "fp32s", "pull", 200, 20, torch, lbm)
+            sub["adjoint_fp32s_128"] = {"mlups": Na * 200 / (msa * 1e-3) / 1e6, "steps": 200, "checkpoint_every": 20,
                                        "launches": la, "mlups_first_call": Na * 200 / (msa1 * 1e-3) / 1e6,
                                        "note": "wall time of lbm_adjoint incl. forward recompute (second call "
                                                "on the same forward run; the first also allocates its buffers)"}
         msE, h2d, d2h = time_e2e(q, n, storage, args.steps, torch, lbm)
         e2e = {"value": N * args.steps * world / (msE * 1e-3) / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-               "note": "per job: one pinned upload of (rho0, u0), init, K steps, moments, one download of u; "
-                       "bytes amortised over the K steps"}
+               "note": "per job: one pinned upload of (rho0, u0), init, K = %d steps, moments, one download "
+                       "of u; bytes amortised over the K steps" % args.steps}
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -507,11 +512,13 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "D3Q19 FP32 256^3 periodic Taylor-Green, u0 0.02, rotated Theta "
-                               "R diag(0.36,0.33,0.30) R^T, tau 0.6",
+                               "R diag(0.36,0.33,0.30) R^T, tau 0.6; populations stored as FP32 f - r_i "
+                               "(the library's default storage), FP32 arithmetic",
                    "cells": N, "l2": "inputs larger than L2 (2 x %.2f GB populations)" % (q * N * 4 / 1e9),
                    "parallelism": "independent replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_source": peak_src, "kernel": "k_step_pull<19, FP32>",
+                     "traffic": traffic, "traffic_source": traffic_note, "peak_source": peak_src,
+                     "kernel": "k_step_pull<19, FP32_SHIFTED>",
                      "bytes_per_cell": bpc, "kernel_ms_mean": kms},
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -68,7 +68,9 @@ typedef void* (*lbm_alloc_fn)(size_t bytes, void* user);
 typedef void (*lbm_free_fn)(void* ptr, void* user);
 
 typedef struct {
-    int storage;              /* enum lbm_storage; default LBM_FP32 */
+    int storage;              /* enum lbm_storage; default LBM_FP32_SHIFTED (plain LBM_FP32
+                                 rounds f ~ w_i instead of f - r_i ~ O(u) and loses about an
+                                 order of magnitude of velocity accuracy at the same speed) */
     int scheme;               /* enum lbm_scheme; default LBM_PULL2 */
     int order;                /* 3 (default, also when 0) or 2: equilibrium truncation order */
     double rho0;              /* reference density of the shifted forms; 0 -> 1.0 */
@@ -240,8 +242,10 @@ int lbm_ade_velocity(lbm_ctx* ctx, void** u);
  * that every GPU loading the library holds until the process exits; every call writes each
  * record it reads, so nothing needs clearing between calls, and all calls share the array:
  * calls that overlap on the GPU (other streams, other host threads) race on it. The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress) and caches it; make
- * that first call outside any stream capture. Any N up to 2^31 - 1 cells fits; larger sizes,
+ * on a device looks up the array's device address (cudaGetSymbolAddress) and caches it for the
+ * life of the process; make that first call outside any stream capture, and do not call this
+ * entry point again after a cudaDeviceReset of that device (the cached address would be stale).
+ * Any N up to 2^31 - 1 cells fits; larger sizes,
  * an unknown lattice, nz != 1 for D2Q9 or null pointers return LBM_ERR_INVALID_ARG. */
 int lbm_totals_noalloc(int lattice, int nx, int ny, int nz, int fp64, const void* f, double* totals, void* stream);
 

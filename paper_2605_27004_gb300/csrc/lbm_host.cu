@@ -435,7 +435,7 @@ extern "C" {
 int lbm_options_default(lbm_options* opt) {
     if (!opt) return LBM_ERR_INVALID_ARG;
     std::memset(opt, 0, sizeof(*opt));
-    opt->storage = LBM_FP32;
+    opt->storage = LBM_FP32_SHIFTED;
     opt->scheme = LBM_PULL2;
     opt->order = 3;
     opt->rho0 = 1.0;

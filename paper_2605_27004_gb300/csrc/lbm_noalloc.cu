@@ -79,7 +79,10 @@ __global__ void __launch_bounds__(kThreads) k_totals_noalloc_finish(const double
     }
 }
 
-// Device address of the scratch array on the current device, looked up once per device.
+// Device address of the scratch array on the current device, looked up once per device. The
+// cached address belongs to the device's primary context as it was at the first call: after a
+// cudaDeviceReset (or anything else that destroys that context) the module is loaded anew and
+// the cached address is stale, so this entry point must not be used across a reset.
 int scratch_for_current_device(double** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -99,14 +102,24 @@ int scratch_for_current_device(double** out) {
     return LBM_OK;
 }
 
+// Both launches go through cudaLaunchKernel, whose return value is the status of that launch
+// alone: an earlier, unrelated error left in the runtime's last-error slot is neither reported
+// as this call's failure nor cleared.
 template <int Q, typename T>
 int launch(const void* f, long long N, double* totals, cudaStream_t s, double* scratch) {
     long long nb = (N + kThreads - 1) / kThreads;
     if (nb > kBlocks) nb = kBlocks;
     if (nb < 1) nb = 1;
-    k_totals_noalloc<Q, T><<<(unsigned)nb, kThreads, 0, s>>>(static_cast<const T*>(f), N, scratch);
-    k_totals_noalloc_finish<<<1, kThreads, 0, s>>>(scratch, (int)nb, totals);
-    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+    const T* fp = static_cast<const T*>(f);
+    void* a1[] = {(void*)&fp, (void*)&N, (void*)&scratch};
+    if (cudaLaunchKernel((const void*)&k_totals_noalloc<Q, T>, dim3((unsigned)nb), dim3(kThreads), a1, 0, s) !=
+        cudaSuccess)
+        return LBM_ERR_CUDA;
+    int nbi = (int)nb;
+    void* a2[] = {(void*)&scratch, (void*)&nbi, (void*)&totals};
+    if (cudaLaunchKernel((const void*)&k_totals_noalloc_finish, dim3(1), dim3(kThreads), a2, 0, s) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    return LBM_OK;
 }
 
 }  // namespace
@@ -115,8 +128,10 @@ extern "C" int lbm_totals_noalloc(int lattice, int nx, int ny, int nz, int fp64,
                                   void* stream) {
     if (lattice != 9 && lattice != 19 && lattice != 27) return LBM_ERR_INVALID_ARG;
     if (nx < 1 || ny < 1 || nz < 1 || (lattice == 9 && nz != 1) || !f || !totals) return LBM_ERR_INVALID_ARG;
-    const long long N = (long long)nx * ny * nz;
-    if (N > 2147483647LL) return LBM_ERR_INVALID_ARG;  // beyond the supported cell count
+    // nx * ny < 2^62 cannot overflow; the product with nz is checked by division first
+    const long long nxy = (long long)nx * ny;
+    if (nxy > 2147483647LL / nz) return LBM_ERR_INVALID_ARG;  // beyond the supported 2^31 - 1 cells
+    const long long N = nxy * nz;
     double* scratch = nullptr;
     int rc = scratch_for_current_device(&scratch);
     if (rc != LBM_OK) return rc;

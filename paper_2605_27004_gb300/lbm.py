@@ -160,7 +160,7 @@ class LBM:
 
     _scalar = False
 
-    def __init__(self, lattice, nx, ny, nz, tau, Theta, solid=None, storage="fp32", scheme="pull", order=3,
+    def __init__(self, lattice, nx, ny, nz, tau, Theta, solid=None, storage="fp32s", scheme="pull", order=3,
                  rho0=1.0, check_every=0, use_graphs=0, device=None, stream=None, torch_alloc=True,
                  adjoint_mem_limit=0):
         torch = _torch()

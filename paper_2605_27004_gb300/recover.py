@@ -24,7 +24,7 @@ from .autograd import simulate, theta_matrix, theta_vector
 CS2 = 1.0 / 3.0
 
 
-def recover_theta(n=128, steps=2000, K=100, iters=50, lr=4e-3, tau=0.6, storage="fp32", seed=inputs.SEED_BASE + 4,
+def recover_theta(n=128, steps=2000, K=100, iters=50, lr=4e-3, tau=0.6, storage="fp32s", seed=inputs.SEED_BASE + 4,
                   log=None):
     dev = torch.device("cuda", torch.cuda.current_device())
     theta_true = theta_vector(inputs.theta_spd(seed + 10))
@@ -63,7 +63,7 @@ def main():
     ap.add_argument("--K", type=int, default=100)
     ap.add_argument("--iters", type=int, default=50)
     ap.add_argument("--lr", type=float, default=4e-3)
-    ap.add_argument("--storage", default="fp32")
+    ap.add_argument("--storage", default="fp32s")
     args = ap.parse_args()
     out = recover_theta(args.n, args.steps, args.K, args.iters, args.lr, storage=args.storage,
                         log=lambda r: print(json.dumps(r), flush=True))

@@ -27,10 +27,13 @@ def rel_l2(a, b):
 
 
 def gpu_run(q, dims, tau, Theta, rho0, u0, steps, solid=None, order=3, storage="fp64", scheme="pull", **kw):
+    """storage=None runs the library's default storage form."""
     import torch
     from paper_2605_27004_gb300 import lbm
     nx, ny, nz = dims
-    L = lbm.LBM(q, nx, ny, nz, tau, Theta, solid=solid, storage=storage, scheme=scheme, order=order, **kw)
+    if storage is not None:
+        kw["storage"] = storage
+    L = lbm.LBM(q, nx, ny, nz, tau, Theta, solid=solid, scheme=scheme, order=order, **kw)
     L.init(torch.as_tensor(rho0), torch.as_tensor(u0))
     L.step(steps)
     rho, u, Pi = L.moments(Pi=True)

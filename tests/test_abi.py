@@ -100,3 +100,15 @@ def test_adjoint_plan_calls_reject_null_context(lib):
     assert lib.lbm_adjoint_info(None, ctypes.byref(k2), ctypes.byref(pf)) == -1
     assert (k2.value, pf.value) == (7, 7)
     assert lib.lbm_adjoint_release(None) == -1
+
+
+def test_default_options_store_shifted_fp32(lib):
+    """The default storage is shifted FP32 (f - r_i), the form that meets the FP32 accuracy bar;
+    plain FP32 is an explicit option."""
+    from paper_2605_27004_gb300 import lbm
+    opt = lbm.lbm_options()
+    assert lib.lbm_options_default(ctypes.byref(opt)) == 0
+    assert opt.storage == lbm.LBM_FP32_SHIFTED
+    assert (opt.scheme, opt.order, opt.rho0) == (lbm.LBM_PULL2, 3, 1.0)
+    import inspect
+    assert inspect.signature(lbm.LBM.__init__).parameters["storage"].default == "fp32s"

@@ -5,8 +5,9 @@ evaluated at Theta = cs2 I (the start of the recovery).
 
 The gradients of the FP64 mode (dL/dTheta for the six independent entries, dL/dtau, dL/du0
 along a random direction) are checked against central finite differences of the library's own
-FP64 forward run, which does not use the adjoint kernels; the FP32-storage gradients (the
-production path, FP32 lambda with FP64 accumulation) against the FP64 ones."""
+FP64 forward run, which does not use the adjoint kernels; the gradients of the default storage
+(shifted FP32, FP32 lambda with FP64 accumulation: the production path) against the FP64 ones
+at 1e-3."""
 import numpy as np
 import pytest
 
@@ -79,10 +80,10 @@ def test_fp32_gradients_match_fp64(problem):
     from paper_2605_27004_gb300.autograd import theta_matrix
     sim64, u0, target, th0 = problem
     _, g64, t64, u64 = _grads(sim64, u0, target, th0, TAU)
-    sim32 = lbm.LBM(19, N3, N3, N3, TAU, theta_matrix(th0, 3), storage="fp32")
+    sim32 = lbm.LBM(19, N3, N3, N3, TAU, theta_matrix(th0, 3))  # default storage: shifted FP32
     _, g32, t32, u32 = _grads(sim32, u0, target, th0, TAU)
     eth = np.abs(g32 - g64).max() / np.abs(g64).max()
     etau = abs(t32 - t64) / abs(t64)
     eu = float((u32 - u64).norm() / u64.norm())
     print(f"FP32 vs FP64: dTheta {eth:.2e}, dtau {etau:.2e}, du0 {eu:.2e}")
-    assert eth < 1e-3 and etau < 1e-2 and eu < 1e-3
+    assert eth < 1e-3 and etau < 1e-3 and eu < 1e-3

@@ -22,7 +22,7 @@ def lib():
 
 
 @pytest.mark.parametrize("q,dims,storage,rtol", [
-    (19, (40, 24, 18), "fp32", 1e-6),   # lbm_totals sums per-cell FP32 moments, this sums FP32 f in FP64
+    (19, (40, 24, 18), "fp32s", 1e-6),  # lbm_totals sums per-cell FP32 moments, this sums FP32 f in FP64
     (27, (23, 17, 12), "fp64", 1e-12),
     (9, (70, 37, 1), "fp64", 1e-12),
 ])
@@ -62,3 +62,8 @@ def test_totals_noalloc_rejects_bad_sizes(lib):
     assert lib.lbm_totals_noalloc(9, 2, 2, 2, 0, p, o, None) == -1
     assert lib.lbm_totals_noalloc(19, 65536, 65536, 1, 0, p, o, None) == -1
     assert lib.lbm_totals_noalloc(11, 2, 2, 2, 0, p, o, None) == -1
+    # products that exceed 2^63 in 64-bit arithmetic are rejected too, not wrapped to a small N
+    assert lib.lbm_totals_noalloc(19, 2 ** 21, 2 ** 21, 2 ** 21, 0, p, o, None) == -1
+    big = 2 ** 31 - 1
+    assert lib.lbm_totals_noalloc(27, big, big, big, 1, p, o, None) == -1
+    assert lib.lbm_totals_noalloc(19, big, 1, 2, 0, p, o, None) == -1
