@@ -13,6 +13,7 @@ Modes
               checkpointed adjoint).
   --mode sweep     one JSON line per variant (lattice x storage x scheme x size, porous runs).
   --mode profile   a small case of one kernel for ncu (--lattice/--storage/--scheme/--n/--kernel).
+  --mode slabs     the z-slab decomposition on one GPU against the whole box (--n, --storage).
   --impl reference the oracle itself timed on the host cores (the reference arm).
 """
 from __future__ import annotations
@@ -32,7 +33,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FALLBACK_HBM_GBS = 6800.0
-ELEM = {"fp32": 4, "fp32s": 4, "fp16s": 2, "fp64": 8}
+ELEM = {"fp32": 4, "fp32s": 4, "fp16s": 2, "fp16w": 2, "fp64": 8}
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the headline kernel from
 # one ncu capture of `python bench.py --mode profile --storage fp32s --n 256`, keyed by variant.
@@ -402,6 +403,50 @@ def run_sweep(args, torch, lbm):
         torch.cuda.empty_cache()
 
 
+def run_slabs(args, torch, lbm):
+    """The z-slab decomposition on one GPU: the whole n^3 Taylor-Green box (D3Q19) against the same
+    box cut into S slabs (one stream and host thread per slab, halo planes exchanged by device
+    copies after every step, the host threads meeting at a barrier per exchange), and one slab
+    of the one-slab-per-process class at world size 1 (its exchange through the same transport
+    function). Wall time over `steps` steps after `warmup`; one JSON line per case."""
+    from paper_2605_27004_gb300 import slabs
+    n = args.n
+    dims, tau, Th, rho0, u0, _ = problem(19, n, "tg")
+    N = int(np.prod(dims))
+    dt = torch.float64 if args.storage == "fp64" else torch.float32
+    r0 = None if rho0 is None else torch.as_tensor(rho0, dtype=dt)
+    u0t = torch.as_tensor(u0, dtype=dt) if not isinstance(u0, torch.Tensor) else u0.to(dt)
+    for S in (1, 2, 4, 8):
+        if S == 1:
+            L = lbm.LBM(19, *dims, tau, Th, storage=args.storage, use_graphs=-1)
+            L.init(r0, u0t)
+            run, close = L.step, L.close
+        else:
+            G = slabs.SlabGroup(19, *dims, tau, Th, S, storage=args.storage)
+            G.init(r0, u0t)
+            run, close = G.step, G.close
+        run(args.warmup)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        run(args.steps)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t) * 1e3
+        close()
+        print(json.dumps({"slabs": S, "n": n, "storage": args.storage, "steps": args.steps, "ms_per_step": ms / args.steps,
+                          "mlups": N * args.steps / (ms * 1e-3) / 1e6,
+                          "case": "whole box" if S == 1 else "SlabGroup, one GPU"}), flush=True)
+        torch.cuda.empty_cache()
+    D = slabs.DistributedSlab(19, *dims, tau, Th, storage=args.storage)
+    D.L.init(None if r0 is None else slabs.slab_of(r0.cuda(), D.plan, dims[0], dims[1]),
+             slabs.slab_of(u0t.cuda().reshape(3, -1), D.plan, dims[0], dims[1]))
+    ms, kms, _ = time_steps(D.L, args.steps, args.warmup, torch)
+    D.L.close()
+    print(json.dumps({"slabs": 1, "n": n, "storage": args.storage, "steps": args.steps, "ms_per_step": ms / args.steps,
+                      "mlups": N * args.steps / (ms * 1e-3) / 1e6,
+                      "case": "DistributedSlab, world size 1 (exchange with itself through the transport)"}),
+          flush=True)
+
+
 def run_profile(args, torch, lbm):
     """Small case for ncu: --kernel fwd runs warmup + steps forward launches; --kernel adjoint
     runs one short adjoint (seed, recompute, adjoint steps)."""
@@ -425,7 +470,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="bench", choices=["bench", "sweep", "profile"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "sweep", "profile", "slabs"])
     ap.add_argument("--no-extras", action="store_true", help="contract line without sub-measurements/e2e/cpu")
     ap.add_argument("--only", default="", help="sweep: substring filter on case names")
     ap.add_argument("--lattice", type=int, default=19)
@@ -453,6 +498,9 @@ def main():
         return
     if args.mode == "profile":
         run_profile(args, torch, lbm)
+        return
+    if args.mode == "slabs":
+        run_slabs(args, torch, lbm)
         return
 
     dist = None

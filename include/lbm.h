@@ -59,7 +59,8 @@ enum lbm_status {
     LBM_ERR_UNSTABLE = -6,    /* a cell reached rho <= 0 or a non-finite value */
     LBM_ERR_NO_FORWARD = -7,  /* adjoint asked for n steps but n steps were not run since init */
     LBM_ERR_TIMEOUT = -8,     /* reserved for bounded device waits (none are used) */
-    LBM_ERR_STATE = -9        /* call out of order (e.g. step before init) */
+    LBM_ERR_STATE = -9,       /* call out of order (e.g. step before init) */
+    LBM_ERR_HALO = -10        /* the halo-exchange callback of a z-slab context failed */
 };
 
 /* Allocator hooks for library-owned device memory (populations, adjoint buffers, checkpoints).
@@ -67,10 +68,20 @@ enum lbm_status {
 typedef void* (*lbm_alloc_fn)(size_t bytes, void* user);
 typedef void (*lbm_free_fn)(void* ptr, void* user);
 
+/* Halo exchange of a z-slab context (see "Z-slab decomposition" below). The library calls it
+ * after every kernel that writes a [q][N] array whose ghost planes a later kernel reads, with
+ * `array` that array (library-owned device memory) and `kind` LBM_HALO_POPULATIONS or
+ * LBM_HALO_ADJOINT. On return the two ghost planes of `array` must hold the neighbouring slabs'
+ * boundary planes (lbm_halo_pack / lbm_halo_unpack), ordered before the next kernel on the
+ * context's stream. Return 0 on success; anything else stops the call with LBM_ERR_HALO. */
+typedef int (*lbm_halo_fn)(struct lbm_ctx* ctx, int kind, void* array, void* user);
+enum lbm_halo_kind { LBM_HALO_POPULATIONS = 0, LBM_HALO_ADJOINT = 1 };
+
 typedef struct {
-    int storage;              /* enum lbm_storage; default LBM_FP32_SHIFTED (plain LBM_FP32
+    int storage;              /* enum lbm_storage; lbm_options_default (and a NULL opt) select
+                                 LBM_FP32_SHIFTED; a zeroed struct selects plain LBM_FP32, which
                                  rounds f ~ w_i instead of f - r_i ~ O(u) and loses about an
-                                 order of magnitude of velocity accuracy at the same speed) */
+                                 order of magnitude of velocity accuracy at the same speed */
     int scheme;               /* enum lbm_scheme; default LBM_PULL2 */
     int order;                /* 3 (default, also when 0) or 2: equilibrium truncation order */
     double rho0;              /* reference density of the shifted forms; 0 -> 1.0 */
@@ -84,6 +95,11 @@ typedef struct {
                                  states of one segment); checkpoints beyond it go to pinned host
                                  memory, segments beyond it are recomputed in two levels;
                                  0: free device memory minus a margin */
+    int z_halo;               /* 1: the context is one z-slab of a larger periodic box (below);
+                                 0: a whole periodic box (default) */
+    lbm_halo_fn halo;         /* z-slab exchange callback; NULL: the slab is the whole box in z
+                                 and its ghost planes are filled from its own boundary planes */
+    void* halo_user;          /* passed to halo */
 } lbm_options;
 
 /* Fill *opt with the defaults (all zero except as documented above). */
@@ -228,6 +244,40 @@ int lbm_ade_set_velocity(lbm_ctx* ctx, const void* u, const double* u_const);
  * velocity, zeros if it was 0) and makes the step read it. The pointer stays valid until
  * lbm_destroy; writes on other streams must be ordered before the next lbm_step. */
 int lbm_ade_velocity(lbm_ctx* ctx, void** u);
+
+/* ---------------------------------------------------------------------------------------------
+ * Z-slab decomposition. Streaming (Eq. LBE_BGK) moves each population one lattice link per step,
+ * so a box split into slabs along z needs, per step, only the populations with c_z = +-1 of the
+ * two planes next to each cut (5 directions per plane for D3Q19, 9 for D3Q27); the reverse
+ * streaming of the adjoint needs the same planes of lambda with the opposite c_z. A context
+ * created with opt->z_halo = 1 holds one slab: `nz` interior planes plus one ghost plane below
+ * (stored plane 0) and one above (stored plane nz + 1), i.e. N = nx*ny*(nz + 2) stored cells.
+ * Every field buffer of such a context (rho, u, Pi, populations, loss_grad, du0, the advecting
+ * velocity) and the solid mask span all N stored cells; kernels read and write the interior
+ * planes only (ghost entries of outputs are left unchanged, of inputs ignored), and the mask's
+ * ghost planes give the solidity of the neighbouring slabs' boundary planes. Totals and
+ * gradients cover the slab's interior; a sharded run sums them over the slabs (FP64).
+ * Restrictions: D3Q19 or D3Q27, the two-array pull scheme, flow contexts (LBM_ERR_INVALID_ARG
+ * otherwise); CUDA graphs are not used. All slabs of one box must run the same sequence of
+ * calls (same n, checkpoint_every and adjoint plan: give them the same adjoint_mem_limit), so
+ * that their halo callbacks pair up.
+ * ------------------------------------------------------------------------------------------- */
+
+/* Bytes of one packed halo plane of `kind` (directions x nx*ny elements; populations in the
+ * storage type, lambda in the field type). LBM_ERR_INVALID_ARG for a context that is not a slab. */
+int lbm_halo_bytes(const lbm_ctx* ctx, int kind, size_t* bytes);
+
+/* Pack the boundary plane that the neighbour on `side` needs (side 0: the lowest interior plane,
+ * sent to the slab below; side 1: the highest, sent to the slab above) from `array` (the device
+ * [q][N] array given to the callback) into the device buffer `buf` of lbm_halo_bytes bytes:
+ * populations with c_z = -1 (side 0) / +1 (side 1), lambda with c_z = +1 (side 0) / -1 (side 1),
+ * in increasing direction order, each an nx*ny plane. Asynchronous on the context's stream. */
+int lbm_halo_pack(lbm_ctx* ctx, int kind, int side, const void* array, void* buf);
+
+/* Unpack a neighbour's packed plane into the ghost plane on `side` of `array` (side 0: the ghost
+ * plane below, filled from the lower slab's side-1 pack; side 1: the ghost plane above, from the
+ * upper slab's side-0 pack). Asynchronous on the context's stream. */
+int lbm_halo_unpack(lbm_ctx* ctx, int kind, int side, void* array, const void* buf);
 
 /* FP64 totals of a caller-owned population array with no device allocation: for callers that
  * cannot call cudaMalloc, cudaFree or any allocating routine where they need the totals (code

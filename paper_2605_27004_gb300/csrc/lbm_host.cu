@@ -23,7 +23,7 @@ Shape shape_for(const Geom& g) {
     const int bx = block_x_for(g.nx);
     const int by = std::max(1, 256 / bx);
     s.block = dim3(bx, by, 1);
-    s.grid = dim3((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
+    s.grid = dim3((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nzp);
     s.nblocks = (long long)s.grid.x * s.grid.y * s.grid.z;
     return s;
 }
@@ -49,6 +49,28 @@ __global__ void __launch_bounds__(1024) k_reduce_partials(const double* __restri
 cudaError_t reduce_partials(const double* partials, long long nb, int width, double* out, cudaStream_t s) {
     k_reduce_partials<<<1, 1024, 0, s>>>(partials, nb, width, out);
     return cudaGetLastError();
+}
+
+// Halo planes of a z-slab: the directions dir[0..n-1] of stored plane `plane` of a [q][N] array,
+// packed as [n][P] (P = nx*ny) into or out of a contiguous buffer.
+struct HaloDirs {
+    int n;
+    int dir[9];
+};
+
+template <typename E>
+__global__ void __launch_bounds__(256) k_halo_copy(E* __restrict__ arr, E* __restrict__ buf, HaloDirs hd, long long N,
+                                                   long long P, long long plane, int pack) {
+    const long long total = (long long)hd.n * P;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(t / P);
+        E* a = arr + (long long)hd.dir[k] * N + plane * P + (t - (long long)k * P);
+        if (pack)
+            buf[t] = *a;
+        else
+            *a = buf[t];
+    }
 }
 
 template <typename T>
@@ -139,6 +161,11 @@ struct lbm_ctx {
     // advection-diffusion: library-owned advecting velocity [d][N] (field type), used unless zero
     void* ade_u = nullptr;
     bool ade_u_zero = true;
+
+    // z-slab: ghost planes 0 and nz + 1 around nz interior planes (geom.z0 = 1)
+    bool slab = false;
+    void* halo_scratch = nullptr;  // two packed planes for the exchange of a slab with itself
+    size_t halo_scratch_bytes = 0;
 
     // graphs
     cudaGraphExec_t graph = nullptr;
@@ -427,6 +454,64 @@ int flow_only(lbm_ctx* c, const char* what) {
     return c->kind == 1 ? fail(c, LBM_ERR_INVALID_ARG, "%s: defined for flow contexts only", what) : LBM_OK;
 }
 
+// --- z-slab halo planes ----------------------------------------------------------------------
+// c_z of the directions a pack on `side` carries: populations stream along +c_i, so the slab
+// below needs the c_z = -1 populations of the lowest interior plane (side 0) and the slab above
+// the c_z = +1 ones of the highest (side 1); lambda streams backwards, so the signs flip. An
+// unpack into the ghost plane on `side` receives what the neighbour on that side packed for its
+// opposite side.
+int halo_sign(int kind, int pack_side) { return (kind == LBM_HALO_POPULATIONS) == (pack_side == 0) ? -1 : 1; }
+
+HaloDirs halo_dirs(int q, int sign) {
+    HaloDirs hd{};
+    for (int i = 0; i < q; ++i)
+        if (velq(q, i).z == sign) hd.dir[hd.n++] = i;
+    return hd;
+}
+
+size_t halo_bytes_of(const lbm_ctx* c, int kind) {
+    const size_t el = kind == LBM_HALO_POPULATIONS ? c->elem : c->felem;
+    return (size_t)halo_dirs(c->q, 1).n * (size_t)c->nx * (size_t)c->ny * el;
+}
+
+cudaError_t halo_copy(lbm_ctx* c, int kind, int side, bool pack, void* array, void* buf) {
+    const HaloDirs hd = halo_dirs(c->q, halo_sign(kind, pack ? side : 1 - side));
+    const long long P = (long long)c->nx * c->ny;
+    const long long plane = pack ? (side == 0 ? 1 : c->nz) : (side == 0 ? 0 : c->nz + 1);
+    const size_t el = kind == LBM_HALO_POPULATIONS ? c->elem : c->felem;
+    const long long total = (long long)hd.n * P;
+    const unsigned nb = (unsigned)std::max<long long>(1, std::min<long long>((total + 255) / 256, 8 * 152));
+    const int pk = pack ? 1 : 0;
+    if (el == 2)
+        k_halo_copy<uint16_t><<<nb, 256, 0, c->stream>>>((uint16_t*)array, (uint16_t*)buf, hd, c->N, P, plane, pk);
+    else if (el == 4)
+        k_halo_copy<uint32_t><<<nb, 256, 0, c->stream>>>((uint32_t*)array, (uint32_t*)buf, hd, c->N, P, plane, pk);
+    else
+        k_halo_copy<uint64_t><<<nb, 256, 0, c->stream>>>((uint64_t*)array, (uint64_t*)buf, hd, c->N, P, plane, pk);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+// Fill the ghost planes of a [q][N] array that the last kernel wrote: through the caller's
+// exchange callback, or, without one, from the slab's own boundary planes (the slab is then the
+// whole box in z, periodic).
+int run_halo(lbm_ctx* c, int kind, void* array) {
+    if (!c->slab) return LBM_OK;
+    if (c->opt.halo) {
+        const int rc = c->opt.halo(c, kind, array, c->opt.halo_user);
+        if (rc != 0) return fail(c, LBM_ERR_HALO, "halo exchange callback returned %d", rc);
+        return LBM_OK;
+    }
+    char* s0 = (char*)c->halo_scratch;
+    char* s1 = s0 + c->halo_scratch_bytes / 2;
+    cudaError_t e = halo_copy(c, kind, 1, true, array, s0);  // top plane -> ghost below
+    if (e == cudaSuccess) e = halo_copy(c, kind, 0, false, array, s0);
+    if (e == cudaSuccess) e = halo_copy(c, kind, 0, true, array, s1);  // bottom plane -> ghost above
+    if (e == cudaSuccess) e = halo_copy(c, kind, 1, false, array, s1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "halo copy");
+    return LBM_OK;
+}
+
 }  // namespace
 
 // =============================================================================================
@@ -454,6 +539,7 @@ const char* lbm_status_string(int s) {
         case LBM_ERR_NO_FORWARD: return "adjoint needs exactly n forward steps since lbm_init";
         case LBM_ERR_TIMEOUT: return "device wait timed out";
         case LBM_ERR_STATE: return "call out of order";
+        case LBM_ERR_HALO: return "halo exchange callback failed";
         default: return "unknown status";
     }
 }
@@ -501,6 +587,7 @@ void lbm_destroy(lbm_ctx* c) {
     dev_free(c, c->gpart, (size_t)c->shape.nblocks * 8 * sizeof(double));
     for (void* p : c->adj_bufs) dev_free(c, p, SB);
     dev_free(c, c->ade_u, (size_t)c->d * c->N * c->felem);
+    dev_free(c, c->halo_scratch, c->halo_scratch_bytes);
     if (c->hout) cudaFreeHost(c->hout);
     if (c->hflag) cudaFreeHost(c->hflag);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -533,11 +620,17 @@ int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau
     c->q = lattice;
     c->d = lattice == 9 ? 2 : 3;
     if (nx < 1 || ny < 1 || nz < 1 || (c->d == 2 && nz != 1)) return bail(LBM_ERR_INVALID_ARG);
+    c->slab = c->opt.z_halo != 0;
+    if (c->slab && (c->d != 3 || c->opt.scheme != LBM_PULL2))
+        return bail(fail(c, LBM_ERR_INVALID_ARG, "z-slab contexts need D3Q19/D3Q27 and the pull scheme"));
+    if (!c->slab && c->opt.halo) return bail(fail(c, LBM_ERR_INVALID_ARG, "halo callback without z_halo"));
+    const int nzs = c->slab ? nz + 2 : nz;  // stored planes
     {
         Geom g0{};
         g0.nx = nx;
         g0.ny = ny;
-        g0.nz = nz;
+        g0.nz = nzs;
+        g0.nzp = nz;
         const Shape s0 = shape_for(g0);
         if (nz > 65535 || s0.grid.y > 65535u) return bail(LBM_ERR_INVALID_ARG);
     }
@@ -547,7 +640,7 @@ int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau
     c->nx = nx;
     c->ny = ny;
     c->nz = nz;
-    c->N = (long long)nx * ny * nz;
+    c->N = (long long)nx * ny * nzs;
     c->tau = tau;
     for (int k = 0; k < c->d * c->d; ++k) c->Theta[k] = Theta[k];
     c->storage = c->opt.storage;
@@ -562,11 +655,14 @@ int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau
     if (c->N >= (1LL << 31)) return bail(fail(c, LBM_ERR_INVALID_ARG, "more than 2^31 - 1 cells"));
     c->geom.nx = nx;
     c->geom.ny = ny;
-    c->geom.nz = nz;
+    c->geom.nz = nzs;
+    c->geom.z0 = c->slab ? 1 : 0;
+    c->geom.nzp = nz;
     c->geom.N = (uint32_t)c->N;
     c->geom.link = nullptr;
     c->shape = shape_for(c->geom);
-    c->n_fluid = c->N;
+    const long long plane = (long long)nx * ny;
+    c->n_fluid = plane * nz;  // interior cells
 
     if (solid_mask) {
         std::vector<uint8_t> m((size_t)c->N);
@@ -577,9 +673,12 @@ int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau
         } else {
             std::memcpy(m.data(), solid_mask, (size_t)c->N);
         }
-        long long nsolid = 0;
-        for (size_t n = 0; n < (size_t)c->N; ++n) nsolid += m[n] != 0;
-        c->n_fluid = c->N - nsolid;
+        long long nsolid = 0, nsolid_int = 0;
+        for (size_t n = 0; n < (size_t)c->N; ++n) {
+            nsolid += m[n] != 0;
+            if (!c->slab || ((long long)n >= plane && (long long)n < plane * (nz + 1))) nsolid_int += m[n] != 0;
+        }
+        c->n_fluid = plane * nz - nsolid_int;
         if (nsolid > 0) {
             c->link = (uint32_t*)dev_alloc(c, (size_t)c->N * 4);
             uint8_t* dmask = (uint8_t*)dev_alloc(c, (size_t)c->N);
@@ -588,6 +687,7 @@ int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau
                 return bail(fail(c, LBM_ERR_OOM, "link-mask allocation"));
             }
             cudaError_t e = cudaMemcpyAsync(dmask, m.data(), (size_t)c->N, cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(c->link, 0, (size_t)c->N * 4, c->stream);  // ghost planes
             if (e == cudaSuccess) e = c->ops->link_mask(c->geom, dmask, c->link, c->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
             dev_free(c, dmask, (size_t)c->N);
@@ -599,6 +699,11 @@ int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau
     c->pop[0] = dev_alloc(c, SB);
     if (c->scheme == LBM_PULL2) c->pop[1] = dev_alloc(c, SB);
     c->flag = (int*)dev_alloc(c, sizeof(int) * 2);
+    if (c->slab) {
+        c->halo_scratch_bytes = 2 * std::max(halo_bytes_of(c, LBM_HALO_POPULATIONS), halo_bytes_of(c, LBM_HALO_ADJOINT));
+        c->halo_scratch = dev_alloc(c, c->halo_scratch_bytes);
+        if (!c->halo_scratch) return bail(fail(c, LBM_ERR_OOM, "halo buffers"));
+    }
     c->partials = (double*)dev_alloc(c, (size_t)c->shape.nblocks * 8 * sizeof(double));
     c->dout = (double*)dev_alloc(c, 8 * sizeof(double));
     if (!c->pop[0] || (c->scheme == LBM_PULL2 && !c->pop[1]) || !c->flag || !c->partials || !c->dout)
@@ -677,7 +782,7 @@ int lbm_step(lbm_ctx* c, int n) {
     if (!c || n < 0) return LBM_ERR_INVALID_ARG;
     if (!c->state_valid) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init");
     const int gsteps = 16;
-    bool graphs = c->opt.use_graphs > 0 || (c->opt.use_graphs == 0 && c->N <= (1LL << 21));
+    bool graphs = !c->slab && (c->opt.use_graphs > 0 || (c->opt.use_graphs == 0 && c->N <= (1LL << 21)));
     long long next_check = c->opt.check_every > 0 ? (c->steps / c->opt.check_every + 1) * c->opt.check_every : -1;
     const bool recording = c->rec_K > 0 && c->rec_valid * c->rec_K > c->steps;
     long long next_rec = recording ? (c->steps / c->rec_K + 1) * c->rec_K : -1;
@@ -698,6 +803,7 @@ int lbm_step(lbm_ctx* c, int n) {
         if (!ran) {
             cudaError_t e = launch_step(c, c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "stream-collide kernel");
+            if (int rc = run_halo(c, LBM_HALO_POPULATIONS, state_ptr(c))) return rc;
             left -= 1;
         }
         if (next_check >= 0 && c->steps >= next_check) {
@@ -856,11 +962,23 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
     }
     void** bufs = c->adj_bufs.data();
     const void* cf = c->coef();
-    auto step_oop = [&](const void* src, void* dst, long long t) -> cudaError_t {
+    // one forward step src -> dst (then the ghost planes of dst, for a z-slab)
+    auto step_oop = [&](const void* src, void* dst, long long t, const char* what) -> int {
         c->launches += 1;
-        if (c->scheme == LBM_PULL2) return c->ops->step_pull(c->geom, cf, src, dst, c->flag, c->stream);
-        return c->ops->step_aa(c->geom, cf, (int)(t & 1), src, dst, c->flag, c->stream);
+        const cudaError_t e = c->scheme == LBM_PULL2
+                                  ? c->ops->step_pull(c->geom, cf, src, dst, c->flag, c->stream)
+                                  : c->ops->step_aa(c->geom, cf, (int)(t & 1), src, dst, c->flag, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, what);
+        return run_halo(c, LBM_HALO_POPULATIONS, dst);
     };
+#define LBM_ADJ_RC(expr)              \
+    do {                              \
+        const int r_ = (expr);        \
+        if (r_ != LBM_OK) {           \
+            release();                \
+            return r_;                \
+        }                             \
+    } while (0)
 
     if (recorded) {
         for (int k = 0; k < C; ++k) {
@@ -901,7 +1019,7 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
             if (t % K == 0)
                 LBM_ADJ_CHECK(cudaMemcpyAsync(ckpt[t / K], bufs[sb], SB, cudaMemcpyDefault, c->stream),
                               "checkpoint copy");
-            LBM_ADJ_CHECK(step_oop(bufs[sb], bufs[sb ^ 1], t), "forward recompute");
+            LBM_ADJ_RC(step_oop(bufs[sb], bufs[sb ^ 1], t, "forward recompute"));
             sb ^= 1;
         }
     }
@@ -956,17 +1074,19 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
     LBM_ADJ_CHECK(c->ops->adj_seed(c->geom, cf, layout_now(c, n), state_ptr(c), loss_grad, c->lam[lc], c->stream),
                   "adjoint seed");
     c->launches += 1;
+    LBM_ADJ_RC(run_halo(c, LBM_HALO_ADJOINT, c->lam[lc]));
     if (cs && ckpt_host[C - 1]) LBM_ADJ_CHECK(prefetch(C - 1), "checkpoint prefetch");
     // adjoint steps t1+len-1 .. t1 over states held in st[0..len-1]
-    auto sweep = [&](const std::vector<const void*>& st, long long t1) -> cudaError_t {
+    auto sweep = [&](const std::vector<const void*>& st, long long t1) -> int {
         for (int j = (int)st.size() - 1; j >= 0; --j) {
-            cudaError_t e = c->ops->adj_step(c->geom, cf, layout_now(c, t1 + j), st[j], c->lam[lc], c->lam[lc ^ 1],
-                                             c->gpart, c->stream);
+            const cudaError_t e = c->ops->adj_step(c->geom, cf, layout_now(c, t1 + j), st[j], c->lam[lc],
+                                                   c->lam[lc ^ 1], c->gpart, c->stream);
             c->launches += 1;
             lc ^= 1;
-            if (e != cudaSuccess) return e;
+            if (e != cudaSuccess) return cuda_fail(c, e, "adjoint step");
+            if (int rc = run_halo(c, LBM_HALO_ADJOINT, c->lam[lc])) return rc;
         }
-        return cudaSuccess;
+        return LBM_OK;
     };
     // Reverse sweep over segments.
     for (int s = C - 1; s >= 0; --s) {
@@ -988,10 +1108,10 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
             std::vector<const void*> st(len);
             st[0] = start;
             for (int j = 1; j < len; ++j) {
-                LBM_ADJ_CHECK(step_oop(st[j - 1], bufs[j], t0 + j - 1), "segment recompute");
+                LBM_ADJ_RC(step_oop(st[j - 1], bufs[j], t0 + j - 1, "segment recompute"));
                 st[j] = bufs[j];
             }
-            LBM_ADJ_CHECK(sweep(st, t0), "adjoint step");
+            LBM_ADJ_RC(sweep(st, t0));
         } else {  // two-level: sub-checkpoints in bufs[1 .. S2-1], sub-segment states after them
             std::vector<const void*> sub(S2);
             sub[0] = start;
@@ -1001,7 +1121,7 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
                 const void* cur = sub[j - 1];
                 for (int i = 1; i <= K2; ++i) {
                     void* dst = i == K2 ? bufs[j] : subseg[i - 1];
-                    LBM_ADJ_CHECK(step_oop(cur, dst, t0 + (long long)(j - 1) * K2 + i - 1), "sub-checkpoint recompute");
+                    LBM_ADJ_RC(step_oop(cur, dst, t0 + (long long)(j - 1) * K2 + i - 1, "sub-checkpoint recompute"));
                     cur = dst;
                 }
                 sub[j] = bufs[j];
@@ -1012,10 +1132,10 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
                 std::vector<const void*> st(len2);
                 st[0] = sub[j];
                 for (int i = 1; i < len2; ++i) {
-                    LBM_ADJ_CHECK(step_oop(st[i - 1], subseg[i - 1], t1 + i - 1), "segment recompute");
+                    LBM_ADJ_RC(step_oop(st[i - 1], subseg[i - 1], t1 + i - 1, "segment recompute"));
                     st[i] = subseg[i - 1];
                 }
-                LBM_ADJ_CHECK(sweep(st, t1), "adjoint step");
+                LBM_ADJ_RC(sweep(st, t1));
             }
         }
     }
@@ -1029,6 +1149,7 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
                   "gradient copy");
     LBM_ADJ_CHECK(cudaStreamSynchronize(c->stream), "adjoint sync");
 #undef LBM_ADJ_CHECK
+#undef LBM_ADJ_RC
     if (c->d == 3) {
         for (int k = 0; k < 6; ++k) c->grad_theta[k] = c->hout[k];
     } else {
@@ -1163,10 +1284,42 @@ int lbm_launch_count(const lbm_ctx* c, long long* launches) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// Z-slab halo planes
+// ---------------------------------------------------------------------------------------------
+int lbm_halo_bytes(const lbm_ctx* c, int kind, size_t* bytes) {
+    if (!c || !bytes || !c->slab || (kind != LBM_HALO_POPULATIONS && kind != LBM_HALO_ADJOINT))
+        return LBM_ERR_INVALID_ARG;
+    *bytes = halo_bytes_of(c, kind);
+    return LBM_OK;
+}
+
+static int halo_call(lbm_ctx* c, int kind, int side, bool pack, void* array, void* buf) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (!c->slab) return fail(c, LBM_ERR_INVALID_ARG, "halo planes exist only in z-slab contexts");
+    if ((kind != LBM_HALO_POPULATIONS && kind != LBM_HALO_ADJOINT) || (side != 0 && side != 1) || !array || !buf)
+        return fail(c, LBM_ERR_INVALID_ARG, "halo %s: bad kind, side or pointer", pack ? "pack" : "unpack");
+    const cudaError_t e = halo_copy(c, kind, side, pack, array, buf);
+    if (e != cudaSuccess) return cuda_fail(c, e, pack ? "halo pack" : "halo unpack");
+    return LBM_OK;
+}
+
+int lbm_halo_pack(lbm_ctx* c, int kind, int side, const void* array, void* buf) {
+    return halo_call(c, kind, side, true, const_cast<void*>(array), buf);
+}
+
+int lbm_halo_unpack(lbm_ctx* c, int kind, int side, void* array, const void* buf) {
+    return halo_call(c, kind, side, false, array, const_cast<void*>(buf));
+}
+
+// ---------------------------------------------------------------------------------------------
 // Anisotropic advection-diffusion of a scalar (lbm_ade.cuh).
 // ---------------------------------------------------------------------------------------------
 int lbm_ade_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau, const double* Theta,
                    const uint8_t* solid_mask, const lbm_options* opt) {
+    if (opt && opt->z_halo) {  // z-slabs are built for the flow only
+        if (out) *out = nullptr;
+        return LBM_ERR_INVALID_ARG;
+    }
     const int rc = lbm_create_ex(out, lattice, nx, ny, nz, tau, Theta, solid_mask, opt);
     if (rc == LBM_OK) (*out)->kind = 1;
     return rc;

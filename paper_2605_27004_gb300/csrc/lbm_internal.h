@@ -7,9 +7,15 @@
 namespace lbm {
 
 // Grid geometry as every kernel sees it. N < 2^31, so in-plane offsets are 32-bit.
+// Every per-cell kernel processes the planes z0 .. z0 + nzp - 1 of the nz stored planes: all of
+// them (z0 = 0, nzp = nz) for a whole periodic box; the interior planes 1 .. nz - 2 of a z-slab
+// whose planes 0 and nz - 1 are ghost copies of the neighbouring slabs' boundary planes
+// (z0 = 1, nzp = nz - 2). Interior cells of a slab never wrap in z, so the wrapped offsets below
+// reach the ghost planes, which the halo exchange fills.
 struct Geom {
     int nx, ny, nz;
-    uint32_t N;            // nx*ny*nz
+    int z0, nzp;           // first processed plane, number of processed planes
+    uint32_t N;            // nx*ny*nz (stored cells, ghost planes included)
     const uint32_t* link;  // per-cell link words or null (all fluid): bit i set when the
                            // neighbour x - c_i is solid, bit 31 set when x itself is solid
 };

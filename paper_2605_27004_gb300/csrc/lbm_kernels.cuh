@@ -125,7 +125,7 @@ struct Cell {
 __device__ __forceinline__ bool make_cell(const Geom& g, Cell& c) {
     c.x = blockIdx.x * blockDim.x + threadIdx.x;
     c.y = blockIdx.y * blockDim.y + threadIdx.y;
-    c.z = blockIdx.z;
+    c.z = blockIdx.z + g.z0;
     if (c.x >= g.nx || c.y >= g.ny) return false;
     const uint32_t yy[3] = {(uint32_t)(c.y + 1 == g.ny ? 0 : c.y + 1), (uint32_t)c.y,
                             (uint32_t)(c.y == 0 ? g.ny - 1 : c.y - 1)};

@@ -109,7 +109,7 @@ __device__ __forceinline__ void make_pcell(const Geom& g, PCell& c) {
     const int px = blockIdx.x * blockDim.x + threadIdx.x;
     c.x0 = 2 * px;
     c.y = blockIdx.y * blockDim.y + threadIdx.y;
-    c.z = blockIdx.z;
+    c.z = blockIdx.z + g.z0;
     c.in_grid = c.x0 < g.nx && c.y < g.ny;
     // clamp out-of-grid lanes to a valid pair so that any address they form is in bounds
     const int x0 = c.in_grid ? c.x0 : 0;
@@ -376,7 +376,7 @@ inline Shape shape_pairs(const Geom& g) {
     const int bx = block_x_for(np);
     const int by = std::max(1, 256 / bx);
     s.block = dim3(bx, by, 1);
-    s.grid = dim3((np + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
+    s.grid = dim3((np + bx - 1) / bx, (g.ny + by - 1) / by, g.nzp);
     s.nblocks = (long long)s.grid.x * s.grid.y * s.grid.z;
     return s;
 }

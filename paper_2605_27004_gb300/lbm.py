@@ -27,20 +27,23 @@ STORAGE = {"fp32": LBM_FP32, "fp64": LBM_FP64, "fp32s": LBM_FP32_SHIFTED, "fp16s
 SCHEME = {"pull": LBM_PULL2, "aa": LBM_AA}
 STATUS = {0: "LBM_OK", -1: "LBM_ERR_INVALID_ARG", -2: "LBM_ERR_NOT_SPD", -3: "LBM_ERR_BAD_TAU",
           -4: "LBM_ERR_OOM", -5: "LBM_ERR_CUDA", -6: "LBM_ERR_UNSTABLE", -7: "LBM_ERR_NO_FORWARD",
-          -8: "LBM_ERR_TIMEOUT", -9: "LBM_ERR_STATE"}
+          -8: "LBM_ERR_TIMEOUT", -9: "LBM_ERR_STATE", -10: "LBM_ERR_HALO"}
+LBM_HALO_POPULATIONS, LBM_HALO_ADJOINT = 0, 1
 D_OF_Q = {9: 2, 19: 3, 27: 3}
 
 # Every exported symbol of the ABI (include/lbm.h), with (restype, argtypes).
 _P, _I, _D, _S, _LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_longlong
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+HALO_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
 
 
 class lbm_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("scheme", ctypes.c_int), ("order", ctypes.c_int),
                 ("rho0", ctypes.c_double), ("check_every", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
-                ("stream", ctypes.c_void_p), ("adjoint_mem_limit", ctypes.c_size_t)]
+                ("stream", ctypes.c_void_p), ("adjoint_mem_limit", ctypes.c_size_t), ("z_halo", ctypes.c_int),
+                ("halo", HALO_FN), ("halo_user", ctypes.c_void_p)]
 
 
 SIGNATURES = {
@@ -68,6 +71,9 @@ SIGNATURES = {
     "lbm_device_bytes": (_I, [_P, ctypes.POINTER(_S)]),
     "lbm_launch_count": (_I, [_P, ctypes.POINTER(_LL)]),
     "lbm_totals_noalloc": (_I, [_I, _I, _I, _I, _I, _P, _P, _P]),
+    "lbm_halo_bytes": (_I, [_P, _I, ctypes.POINTER(_S)]),
+    "lbm_halo_pack": (_I, [_P, _I, _I, _P, _P]),
+    "lbm_halo_unpack": (_I, [_P, _I, _I, _P, _P]),
     "lbm_ade_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _D, _P, _P, ctypes.POINTER(lbm_options)]),
     "lbm_ade_set_velocity": (_I, [_P, _P, _P]),
     "lbm_ade_velocity": (_I, [_P, ctypes.POINTER(_P)]),
@@ -102,10 +108,14 @@ def load(path: str = LIB_PATH):
     return _lib
 
 
-def _check(rc, ctx=None):
+def _check(rc, ctx=None, owner=None):
     if rc != 0:
         lib = load()
         msg = lib.lbm_last_error(ctx).decode() if ctx else lib.lbm_status_string(rc).decode()
+        cause = getattr(owner, "_halo_error", None)
+        if cause is not None:
+            owner._halo_error = None
+            raise LBMError(rc, msg) from cause
         raise LBMError(rc, msg)
     return rc
 
@@ -162,7 +172,10 @@ class LBM:
 
     def __init__(self, lattice, nx, ny, nz, tau, Theta, solid=None, storage="fp32s", scheme="pull", order=3,
                  rho0=1.0, check_every=0, use_graphs=0, device=None, stream=None, torch_alloc=True,
-                 adjoint_mem_limit=0):
+                 adjoint_mem_limit=0, z_halo=False, halo=None):
+        """z_halo: the context is one z-slab of nz interior planes between two ghost planes
+        (fields and the mask then span nx*ny*(nz + 2) cells); halo: the exchange callback
+        halo(kind, array_ptr) of such a slab, or None for a slab that is the whole box in z."""
         torch = _torch()
         lib = load()
         if not torch.cuda.is_available():
@@ -170,7 +183,8 @@ class LBM:
         self.q = int(lattice)
         self.d = D_OF_Q[self.q]
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
-        self.N = self.nx * self.ny * self.nz
+        self.z_halo = bool(z_halo)
+        self.N = self.nx * self.ny * (self.nz + 2 if self.z_halo else self.nz)
         self.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
         self.scheme = SCHEME[scheme] if isinstance(scheme, str) else int(scheme)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -186,6 +200,19 @@ class LBM:
         opt.use_graphs = int(use_graphs)
         opt.stream = ctypes.c_void_p(self.stream.cuda_stream)
         opt.adjoint_mem_limit = int(adjoint_mem_limit)
+        opt.z_halo = int(self.z_halo)
+        self._halo = None
+        self._halo_error = None
+        if halo is not None:
+            def _cb(ctx, kind, array, user):
+                try:
+                    halo(int(kind), int(array or 0))
+                    return 0
+                except BaseException as e:  # reported by the library as LBM_ERR_HALO, re-raised here
+                    self._halo_error = e
+                    return 1
+            self._halo = HALO_FN(_cb)
+            opt.halo = self._halo
         self._alloc = None
         if torch_alloc:
             self._alloc = _TorchAllocator(self.device, self.stream)
@@ -250,7 +277,7 @@ class LBM:
         self._keep = (rho_t, u_t)  # the copies are taken on the stream; keep sources alive
 
     def step(self, n=1):
-        _check(load().lbm_step(self.ctx, int(n)), self.ctx)
+        _check(load().lbm_step(self.ctx, int(n)), self.ctx, self)
 
     def moments(self, rho=True, u=True, Pi=False):
         r = self._empty(self.N) if rho else None
@@ -278,7 +305,7 @@ class LBM:
 
     def adjoint(self, loss_grad, n, checkpoint_every=0):
         g = self._field(loss_grad, (self.d, self.N))
-        _check(load().lbm_adjoint(self.ctx, _ptr(g), int(n), int(checkpoint_every)), self.ctx)
+        _check(load().lbm_adjoint(self.ctx, _ptr(g), int(n), int(checkpoint_every)), self.ctx, self)
 
     def adjoint_info(self):
         """(sub-segment length, host checkpoints prefetched) of the last adjoint."""
@@ -330,6 +357,20 @@ class LBM:
 
     def sync(self):
         _check(load().lbm_sync(self.ctx), self.ctx)
+
+    # -- z-slab halo planes (z_halo contexts) ----------------------------------------------------
+    def halo_bytes(self, kind):
+        b = ctypes.c_size_t()
+        _check(load().lbm_halo_bytes(self.ctx, int(kind), ctypes.byref(b)), self.ctx)
+        return b.value
+
+    def halo_pack(self, kind, side, array, buf):
+        """Pack the boundary plane for the neighbour on `side` of the device array at address
+        `array` (the callback's argument) into the tensor `buf`."""
+        _check(load().lbm_halo_pack(self.ctx, int(kind), int(side), ctypes.c_void_p(array), _ptr(buf)), self.ctx)
+
+    def halo_unpack(self, kind, side, array, buf):
+        _check(load().lbm_halo_unpack(self.ctx, int(kind), int(side), ctypes.c_void_p(array), _ptr(buf)), self.ctx)
 
 
 class _FieldView:
