@@ -234,6 +234,31 @@ def variant(q, n, storage, scheme, kind, steps, warmup, torch, lbm, peak):
             "frac": gbs / peak, "bytes_per_fluid_cell": bpc, "launches": launches}
 
 
+def variant_graphs(q, n, storage, scheme, steps, warmup, torch, lbm, peak):
+    """lbm_step(K) as a caller issues it, one call for all K steps: boxes up to 2M cells replay
+    CUDA graphs of 16 steps (the library's default), larger ones launch step by step. Device time
+    of the call from CUDA events on the context's stream."""
+    L, nf = make_ctx(q, n, storage, scheme, "tg", torch, lbm)
+    K = 16 * max(1, steps // 16)
+    L.step(16 * max(1, warmup))  # the first call captures the graph
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    l0 = L.launches
+    t0.record(L.stream)
+    L.step(K)
+    t1.record(L.stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    launches = L.launches - l0
+    N = L.N
+    L.close()
+    bpc = 2 * q * ELEM[storage]
+    gbs = N * bpc * K / (ms * 1e-3) / 1e9
+    return {"lattice": f"D3Q{q}", "n": n, "storage": storage, "scheme": scheme, "kind": "tg", "via": "lbm_step(K)",
+            "graphs": N <= (1 << 21), "steps": K, "cells": N, "mlups_all": N * K / (ms * 1e-3) / 1e6,
+            "ms_per_step": ms / K, "kernel_gbs": gbs, "frac": gbs / peak, "launches": launches}
+
+
 def time_adjoint(q, n, storage, scheme, steps, K, torch, lbm):
     """Wall time of lbm_adjoint through `steps` steps (forward recompute + reverse sweep), in
     steady state: the second of two calls on the same forward run, as in an optimisation loop
@@ -370,14 +395,27 @@ def run_sweep(args, torch, lbm):
     for c in cases:
         q, n, st, sc, kind = c
         try:
-            r = variant(q, n, st, sc, kind, args.steps, args.warmup, torch, lbm, peak)
+            with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+                r = variant(q, n, st, sc, kind, args.steps, args.warmup, torch, lbm, peak)
             r["peak"] = peak
             r["peak_source"] = src
+            r["clocks"] = clk.summary()
         except Exception as e:  # report and continue (e.g. memory)
             r = {"case": c, "error": str(e)[:200]}
         print(json.dumps(r), flush=True)
         torch.cuda.empty_cache()
-    for (q, n, st, sc, K, steps) in [(19, 128, "fp32s", "pull", 20, 200), (19, 128, "fp16s", "pull", 20, 200),
+    for (q, n, st, sc) in [(19, 64, "fp32s", "pull"), (19, 64, "fp16s", "pull"), (19, 64, "fp16s", "aa"),
+                           (19, 128, "fp32s", "pull"), (19, 128, "fp16s", "pull"), (19, 128, "fp16s", "aa")]:
+        if args.only and args.only not in "graphs_%d_%d_%s_%s" % (q, n, st, sc):
+            continue
+        try:
+            r = variant_graphs(q, n, st, sc, max(args.steps, 64), args.warmup, torch, lbm, peak)
+            r["peak"] = peak
+        except Exception as e:
+            r = {"graphs": True, "case": [q, n, st, sc], "error": str(e)[:200]}
+        print(json.dumps(r), flush=True)
+    for (q, n, st, sc, K, steps) in [(19, 64, "fp32s", "pull", 20, 200), (19, 64, "fp16s", "aa", 20, 200),
+                                     (19, 128, "fp32s", "pull", 20, 200), (19, 128, "fp16s", "pull", 20, 200),
                                      (19, 256, "fp32s", "pull", 20, 100), (19, 256, "fp16s", "aa", 20, 100),
                                      (19, 512, "fp16s", "aa", 20, 200), (19, 768, "fp16s", "aa", 20, 200)]:
         if args.only and args.only not in "adj_%d_%d_%s_%s" % (q, n, st, sc):

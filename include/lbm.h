@@ -43,8 +43,11 @@ enum lbm_lattice { LBM_D2Q9 = 9, LBM_D3Q19 = 19, LBM_D3Q27 = 27 };
 
 /* Population storage. Arithmetic is FP32 except in LBM_FP64. Shifted forms store
  * f_i - r_i with r_i = feq_i(rho0, u = 0; Theta) = w_i rho0 (1 + h_i/(2 cs2^2)), the rest
- * equilibrium (equals w_i rho0 when Theta = cs2 I). */
-enum lbm_storage { LBM_FP32 = 0, LBM_FP64 = 1, LBM_FP32_SHIFTED = 2, LBM_FP16_SHIFTED = 3 };
+ * equilibrium (equals w_i rho0 when Theta = cs2 I). LBM_FP16_WSHIFTED stores f_i - w_i rho0 in
+ * FP16, the shift by the lattice weights alone: when Theta != cs2 I its stored values carry the
+ * offset r_i - w_i rho0 as well, which costs FP16 precision; it is kept as the comparison
+ * (ablation) for LBM_FP16_SHIFTED, runs one cell per thread, and is not meant for production. */
+enum lbm_storage { LBM_FP32 = 0, LBM_FP64 = 1, LBM_FP32_SHIFTED = 2, LBM_FP16_SHIFTED = 3, LBM_FP16_WSHIFTED = 4 };
 
 /* Streaming schemes: two arrays in pull form, or one array in the AA pattern (in place). */
 enum lbm_scheme { LBM_PULL2 = 0, LBM_AA = 1 };

@@ -1,8 +1,8 @@
 """Build of the CUDA library ``_build/liblbm.so`` for sm_103a (nvcc, no cmake).
 
-lbm_ops.cu is compiled once per (lattice, storage) pair and lbm_host.cu once; the thirteen
-objects build in parallel and link against the shared CUDA runtime, which the process shares
-with PyTorch.
+lbm_ops.cu is compiled once per (lattice, storage) pair and once more per 3D pair for z-slab
+contexts, lbm_host.cu and lbm_noalloc.cu once; the twenty-seven objects build in parallel and
+link against the shared CUDA runtime, which the process shares with PyTorch.
 """
 from __future__ import annotations
 
@@ -21,7 +21,8 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing"]
 LATTICES = (9, 19, 27)
-STORAGES = (0, 1, 2, 3)
+STORAGES = (0, 1, 2, 3, 4)
+SLAB_LATTICES = (19, 27)
 
 
 def _nvcc() -> str:
@@ -62,6 +63,11 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
         for s in STORAGES:
             obj = os.path.join(OUT, f"lbm_ops_q{q}_s{s}.o")
             tasks.append([nvcc, *ARCH, *FLAGS, f"-DLBM_Q={q}", f"-DLBM_S={s}", "-c",
+                          os.path.join(CSRC, "lbm_ops.cu"), "-o", obj])
+    for q in SLAB_LATTICES:  # the same kernels with the first processed plane at 1 (z-slabs)
+        for s in STORAGES:
+            obj = os.path.join(OUT, f"lbm_ops_q{q}_s{s}_slab.o")
+            tasks.append([nvcc, *ARCH, *FLAGS, f"-DLBM_Q={q}", f"-DLBM_S={s}", "-DLBM_SLAB=1", "-c",
                           os.path.join(CSRC, "lbm_ops.cu"), "-o", obj])
     for name in ("lbm_host", "lbm_noalloc"):
         tasks.append([nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, name + ".cu"), "-o",

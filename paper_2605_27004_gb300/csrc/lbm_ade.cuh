@@ -18,6 +18,7 @@
 #include "lbm_kernels.cuh"
 
 namespace lbm {
+inline namespace LBM_VARIANT {
 
 template <typename T>
 struct VelField {
@@ -51,12 +52,15 @@ __global__ void __launch_bounds__(256)
     Cell c;
     if (!make_cell(g, c)) return;
     const uint32_t lw = link_of<MASK>(g, c);
-    // with walls, solid lanes of a warp that holds a fluid cell store zeros into their own
+    // with walls, solid lanes of a sector that holds a fluid cell store zeros into their own
     // (never read) slots, so that destination sectors are written whole (as in k_step_pull)
     const bool solid = MASK && (lw & LINK_SOLID);
-    if (MASK && __all_sync(__activemask(), solid)) return;
+    const unsigned act = __activemask();
+    if (MASK && __all_sync(act, solid)) return;
     T d[Q];
-    if (!solid) {
+    if (MASK && __all_sync(act, lw == 0u)) {  // no wall link in the warp (see k_step_pull)
+        gather<Q, S, false, LAYOUT_PULL, true>(c, 0u, cf, src, d);
+    } else if (!solid) {
         gather<Q, S, MASK, LAYOUT_PULL, true>(c, lw, cf, src, d);
     } else {
 #pragma unroll
@@ -64,8 +68,9 @@ __global__ void __launch_bounds__(256)
     }
     const T s = ade_bgk<Q, T>(cf, vf, c.n, d);
     if (!solid && !isfinite(s)) *flag = 1;
+    if (MASK && !store_group<typename Store<S>::type>(act, solid)) return;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st_raw(dst.p[i] + c.n, solid ? T(0) : from_shifted<S>(d[i], cf.r[i]));
+    for (int i = 0; i < Q; ++i) st_raw(dst.p[i] + c.n, solid ? T(0) : from_shifted<S>(d[i], cf.so[i]));
 }
 
 // AA pattern in place (see k_step_aa): even steps read and write the own cell, odd steps the
@@ -81,13 +86,24 @@ __global__ void __launch_bounds__(256)
     const uint32_t lw = link_of<MASK>(g, c);
     if (MASK && (lw & LINK_SOLID)) return;
     T d[Q];
-    if (ODD)
+    const bool clean = MASK && __all_sync(__activemask(), lw == 0u);  // see k_step_aa
+    if (clean) {
+        if (ODD)
+            gather<Q, S, false, LAYOUT_AAODD, false>(c, 0u, cf, src, d);
+        else
+            gather<Q, S, false, LAYOUT_LOCAL, false>(c, 0u, cf, src, d);
+    } else if (ODD) {
         gather<Q, S, MASK, LAYOUT_AAODD, false>(c, lw, cf, src, d);
-    else
+    } else {
         gather<Q, S, MASK, LAYOUT_LOCAL, false>(c, lw, cf, src, d);
+    }
     const T s = ade_bgk<Q, T>(cf, vf, c.n, d);
     if (!isfinite(s)) *flag = 1;
-    aa_store<Q, S, MASK, ODD>(c, lw, cf, dst, d);
+    if (clean)
+        aa_store<Q, S, false, ODD>(c, 0u, cf, dst, d);
+    else
+        aa_store<Q, S, MASK, ODD>(c, lw, cf, dst, d);
 }
 
+}  // namespace LBM_VARIANT
 }  // namespace lbm

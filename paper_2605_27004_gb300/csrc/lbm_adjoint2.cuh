@@ -10,6 +10,7 @@
 #include "lbm_pairs.cuh"
 
 namespace lbm {
+inline namespace LBM_VARIANT {
 
 // lambda_(t+1),i at x0 + c_i and x0 + 1 + c_i (reverse gather), row of x + c_i at `row`
 __device__ __forceinline__ F2 gather_lam(const float* p, uint32_t row, const PCell& c, int cx, int nx) {
@@ -35,11 +36,11 @@ __global__ void __launch_bounds__(256, 2)
             const Vec3 v = vel<Q>(i);
             mu[i] = gather_lam(lam_next.p[i], c.R[1 - v.y][1 - v.z], c, v.x, g.nx);
             if (LAYOUT == LAYOUT_LOCAL)
-                dk[i] = to_shifted2<S>(ld2(src.p[i] + c.n), cf.r[i]);
+                dk[i] = to_shifted2<S>(ld2(src.p[i] + c.n), cf.so[i]);
             else if (LAYOUT == LAYOUT_PULL)
-                dk[i] = gather_pair<S, true>(src.p[i], c.R[v.y + 1][v.z + 1], c, v.x, g.nx, cf.r[i]);
+                dk[i] = gather_pair<S, true>(src.p[i], c.R[v.y + 1][v.z + 1], c, v.x, g.nx, cf.so[i]);
             else
-                dk[i] = gather_pair<S, true>(src.p[opp(i)], c.R[v.y + 1][v.z + 1], c, v.x, g.nx, cf.r[i]);
+                dk[i] = gather_pair<S, true>(src.p[opp(i)], c.R[v.y + 1][v.z + 1], c, v.x, g.nx, cf.so[i]);
         }
         // moments of f_t
         F2 drho = dk[0], jx = f2(0.f), jy = f2(0.f), jz = f2(0.f);
@@ -185,4 +186,5 @@ __global__ void __launch_bounds__(256, 2)
     accumulate_record<float>(rec, gpart);
 }
 
+}  // namespace LBM_VARIANT
 }  // namespace lbm

@@ -18,12 +18,12 @@
 
 namespace lbm {
 
-Shape shape_for(const Geom& g) {
+Shape shape_for(const Geom& g, int nzp) {
     Shape s;
     const int bx = block_x_for(g.nx);
     const int by = std::max(1, 256 / bx);
     s.block = dim3(bx, by, 1);
-    s.grid = dim3((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nzp);
+    s.grid = dim3((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, nzp);
     s.nblocks = (long long)s.grid.x * s.grid.y * s.grid.z;
     return s;
 }
@@ -79,18 +79,24 @@ __global__ void k_fill(T* __restrict__ p, long long n, T v) {
         p[i] = v;
 }
 
-static const Ops* ops_get(int q, int storage) {
-#define LBM_PICK(Q)                              \
+static const Ops* ops_get(int q, int storage, bool slab) {
+#define LBM_PICK(Q, SUF)                         \
     switch (storage) {                           \
-        case 0: return &ops_q##Q##_s0();         \
-        case 1: return &ops_q##Q##_s1();         \
-        case 2: return &ops_q##Q##_s2();         \
-        case 3: return &ops_q##Q##_s3();         \
+        case 0: return &ops_q##Q##_s0##SUF();    \
+        case 1: return &ops_q##Q##_s1##SUF();    \
+        case 2: return &ops_q##Q##_s2##SUF();    \
+        case 3: return &ops_q##Q##_s3##SUF();    \
+        case 4: return &ops_q##Q##_s4##SUF();    \
         default: return nullptr;                 \
     }
-    if (q == 9) LBM_PICK(9)
-    if (q == 19) LBM_PICK(19)
-    if (q == 27) LBM_PICK(27)
+    if (slab) {  // z-slab objects exist for the 3D lattices
+        if (q == 19) LBM_PICK(19, _slab)
+        if (q == 27) LBM_PICK(27, _slab)
+        return nullptr;
+    }
+    if (q == 9) LBM_PICK(9, )
+    if (q == 19) LBM_PICK(19, )
+    if (q == 27) LBM_PICK(27, )
 #undef LBM_PICK
     return nullptr;
 }
@@ -299,6 +305,8 @@ void build_coef(lbm_ctx* c) {
         C.h[i] = h;
         C.A[i] = w * (1.0 + 4.5 * h);
         C.r[i] = rho0 * C.A[i];
+        C.so[i] = c->storage == LBM_FP16_WSHIFTED ? C.r[i] - w * rho0
+                  : (c->storage == LBM_FP32 || c->storage == LBM_FP64) ? C.r[i] : 0.0;
         C.B[i] = w * (3.0 + 3.0 * C.c3 * h);
         for (int k = 0; k < 6; ++k) C.Pirest[k] += C.r[i] * cv[pa[k]] * cv[pb[k]];
     }
@@ -312,6 +320,7 @@ void build_coef(lbm_ctx* c) {
     }
     for (int i = 0; i < 27; ++i) {
         F.r[i] = (float)C.r[i];
+        F.so[i] = (float)C.so[i];
         F.A[i] = (float)C.A[i];
         F.B[i] = (float)C.B[i];
         F.h[i] = (float)C.h[i];
@@ -613,7 +622,7 @@ int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau
     if (c->opt.order == 0) c->opt.order = 3;
     if (c->opt.rho0 == 0.0) c->opt.rho0 = 1.0;
     if (lattice != 9 && lattice != 19 && lattice != 27) return bail(LBM_ERR_INVALID_ARG);
-    if (c->opt.storage < 0 || c->opt.storage > 3 || c->opt.scheme < 0 || c->opt.scheme > 1) return bail(LBM_ERR_INVALID_ARG);
+    if (c->opt.storage < 0 || c->opt.storage > 4 || c->opt.scheme < 0 || c->opt.scheme > 1) return bail(LBM_ERR_INVALID_ARG);
     if (c->opt.order != 2 && c->opt.order != 3) return bail(LBM_ERR_INVALID_ARG);
     if (!(c->opt.rho0 > 0.0) || !std::isfinite(c->opt.rho0)) return bail(LBM_ERR_INVALID_ARG);
     if ((c->opt.alloc == nullptr) != (c->opt.free == nullptr)) return bail(LBM_ERR_INVALID_ARG);
@@ -630,8 +639,7 @@ int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau
         g0.nx = nx;
         g0.ny = ny;
         g0.nz = nzs;
-        g0.nzp = nz;
-        const Shape s0 = shape_for(g0);
+        const Shape s0 = shape_for(g0, nz);
         if (nz > 65535 || s0.grid.y > 65535u) return bail(LBM_ERR_INVALID_ARG);
     }
     if (!(tau > 0.5) || !std::isfinite(tau)) return bail(LBM_ERR_BAD_TAU);
@@ -646,9 +654,9 @@ int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau
     c->storage = c->opt.storage;
     c->scheme = c->opt.scheme;
     c->order = c->opt.order;
-    c->elem = c->storage == LBM_FP64 ? 8 : c->storage == LBM_FP16_SHIFTED ? 2 : 4;
+    c->elem = c->storage == LBM_FP64 ? 8 : (c->storage == LBM_FP16_SHIFTED || c->storage == LBM_FP16_WSHIFTED) ? 2 : 4;
     c->felem = c->storage == LBM_FP64 ? 8 : 4;
-    c->ops = ops_get(c->q, c->storage);
+    c->ops = ops_get(c->q, c->storage, c->slab);
     c->stream = (cudaStream_t)c->opt.stream;
     build_coef(c);
 
@@ -656,11 +664,9 @@ int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau
     c->geom.nx = nx;
     c->geom.ny = ny;
     c->geom.nz = nzs;
-    c->geom.z0 = c->slab ? 1 : 0;
-    c->geom.nzp = nz;
     c->geom.N = (uint32_t)c->N;
     c->geom.link = nullptr;
-    c->shape = shape_for(c->geom);
+    c->shape = shape_for(c->geom, nz);
     const long long plane = (long long)nx * ny;
     c->n_fluid = plane * nz;  // interior cells
 
@@ -928,8 +934,10 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
     std::vector<bool> own_host;
     cudaStream_t cs = nullptr;  // copy stream of the checkpoint prefetch
     cudaEvent_t ev_free = nullptr, ev_done[2] = {nullptr, nullptr};
+    cudaGraphExec_t seg_graph = nullptr;  // one full segment, replayed (small boxes)
     auto release = [&]() {
         cudaStreamSynchronize(c->stream);
+        if (seg_graph) cudaGraphExecDestroy(seg_graph);
         if (cs) {
             cudaStreamSynchronize(cs);
             cudaStreamDestroy(cs);
@@ -1088,6 +1096,45 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
         }
         return LBM_OK;
     };
+    // Small boxes are launch-bound: a full segment of a flat plan (K - 1 recompute steps and K
+    // adjoint steps over the same buffers) is captured once as a CUDA graph and replayed for
+    // every full segment, its start state first copied into bufs[0]. That needs the same lambda
+    // and AA parities at every segment start (K even), device checkpoints only (bufs[0] is then
+    // not a restore target), and no halo callbacks between the kernels.
+    int n_host_ckpt = 0;
+    for (int k = 0; k < C; ++k) n_host_ckpt += ckpt_host[k] ? 1 : 0;
+    const bool seg_graphs = K2 >= K && K % 2 == 0 && K >= 2 && n_host_ckpt == 0 && !c->slab &&
+                            (c->opt.use_graphs > 0 || (c->opt.use_graphs == 0 && c->N <= (1LL << 21)));
+    auto capture_segment = [&](long long t0) -> int {
+        if (!c->cap_stream) LBM_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        LBM_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int j = 1; j < K && e == cudaSuccess; ++j)
+            e = c->scheme == LBM_PULL2
+                    ? c->ops->step_pull(c->geom, cf, bufs[j - 1], bufs[j], c->flag, c->cap_stream)
+                    : c->ops->step_aa(c->geom, cf, (int)((t0 + j - 1) & 1), bufs[j - 1], bufs[j], c->flag,
+                                      c->cap_stream);
+        int l = lc;
+        for (int j = K - 1; j >= 0 && e == cudaSuccess; --j) {
+            e = c->ops->adj_step(c->geom, cf, layout_now(c, t0 + j), bufs[j], c->lam[l], c->lam[l ^ 1], c->gpart,
+                                 c->cap_stream);
+            l ^= 1;
+        }
+        cudaGraph_t gr = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &gr);
+        if (e != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            return cuda_fail(c, e, "kernel launch during segment capture");
+        }
+        if (ee != cudaSuccess) return cuda_fail(c, ee, "cudaStreamEndCapture (segment)");
+        const cudaError_t ie = cudaGraphInstantiate(&seg_graph, gr, 0);
+        cudaGraphDestroy(gr);
+        if (ie != cudaSuccess) {
+            seg_graph = nullptr;
+            return cuda_fail(c, ie, "cudaGraphInstantiate (segment)");
+        }
+        return LBM_OK;
+    };
     // Reverse sweep over segments.
     for (int s = C - 1; s >= 0; --s) {
         const long long t0 = (long long)s * K;
@@ -1104,7 +1151,14 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
             }
         }
         if (cs && s > 0 && ckpt_host[s - 1]) LBM_ADJ_CHECK(prefetch(s - 1), "checkpoint prefetch");
-        if (K2 >= K) {  // flat: states t0 + j in bufs[j], j = 1 .. len-1
+        if (seg_graphs && len == K) {
+            if (start != bufs[0])
+                LBM_ADJ_CHECK(cudaMemcpyAsync(bufs[0], start, SB, cudaMemcpyDeviceToDevice, c->stream),
+                              "segment start copy");
+            if (!seg_graph) LBM_ADJ_RC(capture_segment(t0));
+            LBM_ADJ_CHECK(cudaGraphLaunch(seg_graph, c->stream), "segment graph launch");
+            c->launches += 2 * K - 1;  // K even: lc is back at its value at the segment start
+        } else if (K2 >= K) {  // flat: states t0 + j in bufs[j], j = 1 .. len-1
             std::vector<const void*> st(len);
             st[0] = start;
             for (int j = 1; j < len; ++j) {

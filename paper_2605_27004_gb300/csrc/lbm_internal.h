@@ -7,14 +7,14 @@
 namespace lbm {
 
 // Grid geometry as every kernel sees it. N < 2^31, so in-plane offsets are 32-bit.
-// Every per-cell kernel processes the planes z0 .. z0 + nzp - 1 of the nz stored planes: all of
-// them (z0 = 0, nzp = nz) for a whole periodic box; the interior planes 1 .. nz - 2 of a z-slab
-// whose planes 0 and nz - 1 are ghost copies of the neighbouring slabs' boundary planes
-// (z0 = 1, nzp = nz - 2). Interior cells of a slab never wrap in z, so the wrapped offsets below
-// reach the ghost planes, which the halo exchange fills.
+// Every per-cell kernel processes the stored planes z0 .. nz - 1 - z0: all of them for a whole
+// periodic box (z0 = 0); for a z-slab (z0 = 1) the interior planes between ghost plane 0 and ghost
+// plane nz - 1, which hold the neighbouring slabs' boundary planes. Interior cells of a slab never
+// wrap in z, so the wrapped offsets reach the ghost planes, which the halo exchange fills. z0 is
+// not a field: each kernel object is compiled for one value (LBM_SLAB in the kernel headers; as a
+// kernel parameter it changed the register allocation of the FP16 pair kernels).
 struct Geom {
     int nx, ny, nz;
-    int z0, nzp;           // first processed plane, number of processed planes
     uint32_t N;            // nx*ny*nz (stored cells, ghost planes included)
     const uint32_t* link;  // per-cell link words or null (all fluid): bit i set when the
                            // neighbour x - c_i is solid, bit 31 set when x itself is solid
@@ -30,6 +30,8 @@ struct Coef {
     T c3;         // 9/2 for the third-order equilibrium, 0 for the second order
     T K[6];       // K~ = Theta - cs2 I: xx, yy, zz, xy, xz, yz
     T r[27];      // rest equilibrium r_i = w_i rho0 (1 + 9/2 h_i)
+    T so[27];     // storage offset: stored value = f_i - r_i + so_i (so = r for plain storage,
+                  // 0 for the r-shifted forms, r_i - w_i rho0 for the w-shifted FP16 form)
     T A[27];      // w_i (1 + 9/2 h_i): density coefficient of the even part
     T B[27];      // w_i (3 + 3 c3 h_i): linear coefficient of the odd part
     T h[27];      // h_i = c_i.K~.c_i - cs2 tr K~
@@ -42,12 +44,13 @@ struct Coef {
 //   AAODD  f_i(x) = A[opp i][x - c_i], or A[i][x] if x - c_i is solid (AA, odd step count)
 enum Layout { LAYOUT_LOCAL = 0, LAYOUT_PULL = 1, LAYOUT_AAODD = 2 };
 
-// Launch shape shared by every per-cell kernel: 256-thread blocks, x fastest.
+// Launch shape shared by every per-cell kernel: 256-thread blocks, x fastest, one grid plane per
+// processed lattice plane (nzp of them).
 struct Shape {
     dim3 grid, block;
     long long nblocks;
 };
-Shape shape_for(const Geom& g);
+Shape shape_for(const Geom& g, int nzp);
 
 // Block width for n threads along x: a multiple of 32 up to 256 that wastes the fewest threads
 // in the last block of a row; among those, a divisor of 256 (so that blocks of bx x 256/bx
@@ -98,11 +101,12 @@ struct Ops {
                           int* flag, cudaStream_t);
 };
 
-// One translation unit per (lattice, storage): lbm_ops.cu compiled with LBM_Q / LBM_S.
-#define LBM_OPS_DECL(Q, S) const Ops& ops_q##Q##_s##S();
-LBM_OPS_DECL(9, 0) LBM_OPS_DECL(9, 1) LBM_OPS_DECL(9, 2) LBM_OPS_DECL(9, 3)
-LBM_OPS_DECL(19, 0) LBM_OPS_DECL(19, 1) LBM_OPS_DECL(19, 2) LBM_OPS_DECL(19, 3)
-LBM_OPS_DECL(27, 0) LBM_OPS_DECL(27, 1) LBM_OPS_DECL(27, 2) LBM_OPS_DECL(27, 3)
+// One translation unit per (lattice, storage): lbm_ops.cu compiled with LBM_Q / LBM_S, and for
+// D3Q19 / D3Q27 once more with LBM_SLAB = 1 for z-slab contexts (ops_q<Q>_s<S>_slab).
+#define LBM_OPS_DECL(Q, S) const Ops& ops_q##Q##_s##S(); const Ops& ops_q##Q##_s##S##_slab();
+const Ops& ops_q9_s0(); const Ops& ops_q9_s1(); const Ops& ops_q9_s2(); const Ops& ops_q9_s3(); const Ops& ops_q9_s4();
+LBM_OPS_DECL(19, 0) LBM_OPS_DECL(19, 1) LBM_OPS_DECL(19, 2) LBM_OPS_DECL(19, 3) LBM_OPS_DECL(19, 4)
+LBM_OPS_DECL(27, 0) LBM_OPS_DECL(27, 1) LBM_OPS_DECL(27, 2) LBM_OPS_DECL(27, 3) LBM_OPS_DECL(27, 4)
 #undef LBM_OPS_DECL
 
 // Deterministic FP64 sum of `nb` partial records of `width` doubles into out[width]

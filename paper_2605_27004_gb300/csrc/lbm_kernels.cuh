@@ -32,10 +32,27 @@
 #include "lbm_internal.h"
 #include "lbm_lattice.cuh"
 
+// Each kernel object is compiled for whole periodic boxes (LBM_SLAB = 0) or for z-slabs
+// (LBM_SLAB = 1, the processed planes start at stored plane 1, above the ghost plane). The first
+// processed plane is a compile-time constant: read from the kernel parameters it changed the
+// register allocation of the FP16 pair kernels and cost them up to 18 % (measured). The two
+// builds live in different inline namespaces, so their template instantiations never collide.
+#ifndef LBM_SLAB
+#define LBM_SLAB 0
+#endif
+#if LBM_SLAB
+#define LBM_VARIANT slab_planes
+#else
+#define LBM_VARIANT whole_box
+#endif
+
 namespace lbm {
+inline namespace LBM_VARIANT {
 
 // ---------------------------------------------------------------------------------------------
-// Storage forms: 0 FP32 (f), 1 FP64 (f), 2 FP32 shifted (f - r), 3 FP16 shifted (f - r).
+// Storage forms: 0 FP32 (f), 1 FP64 (f), 2 FP32 shifted (f - r), 3 FP16 shifted (f - r),
+// 4 FP16 shifted by the lattice weights (f - w rho0). The arithmetic always runs on d = f - r; the
+// forms whose stored value is not d convert with the storage offset Coef::so on load and store.
 // ---------------------------------------------------------------------------------------------
 template <int S>
 struct Store;
@@ -70,6 +87,17 @@ struct Store<3> {
     static constexpr bool shifted = true;
     static constexpr bool fix_momentum = false;  // FP16 rounding (1e-3) dwarfs the 1e-8 bias
     static constexpr bool fold_omega = true;     // see relax()
+};
+// FP16 storage of f - w rho0, the shift taken literally from the lattice weights: stored values
+// carry r_i - w_i rho0 = 9/2 w_i rho0 h_i on top of the O(u) deviation when Theta != cs2 I. It
+// exists to measure what the Theta-aware shift of Store<3> gains; one cell per thread only.
+template <>
+struct Store<4> {
+    using type = __half;
+    using T = float;
+    static constexpr bool shifted = false;
+    static constexpr bool fix_momentum = false;
+    static constexpr bool fold_omega = true;
 };
 
 // read-only (non-coherent) loads: used when the source array is not written by the kernel
@@ -118,6 +146,7 @@ Planes<P> planes_of(P* base, int q, uint32_t N) {
 struct Cell {
     int x, y, z;
     uint32_t n;
+    uint32_t N;  // cells per population plane
     uint32_t X[3];
     uint32_t R[3][3];
 };
@@ -125,7 +154,7 @@ struct Cell {
 __device__ __forceinline__ bool make_cell(const Geom& g, Cell& c) {
     c.x = blockIdx.x * blockDim.x + threadIdx.x;
     c.y = blockIdx.y * blockDim.y + threadIdx.y;
-    c.z = blockIdx.z + g.z0;
+    c.z = blockIdx.z + LBM_SLAB;
     if (c.x >= g.nx || c.y >= g.ny) return false;
     const uint32_t yy[3] = {(uint32_t)(c.y + 1 == g.ny ? 0 : c.y + 1), (uint32_t)c.y,
                             (uint32_t)(c.y == 0 ? g.ny - 1 : c.y - 1)};
@@ -140,6 +169,7 @@ __device__ __forceinline__ bool make_cell(const Geom& g, Cell& c) {
 #pragma unroll
         for (int b = 0; b < 3; ++b) c.R[a][b] = nx * (yy[a] + ny * zz[b]);
     c.n = c.X[1] + c.R[1][1];
+    c.N = g.N;
     return true;
 }
 
@@ -166,13 +196,21 @@ __device__ __forceinline__ void gather(const Cell& c, uint32_t lw, const Coef<ty
         } else {
             const int slot_n = LAYOUT == LAYOUT_PULL ? i : opp(i);  // slot read from the neighbour
             const int slot_w = LAYOUT == LAYOUT_PULL ? opp(i) : i;  // slot read on a wall link
-            if (MASK && link_bit(lw, i))
-                p = src.p[slot_w] + c.n;
-            else
+            if (MASK) {
+                // Both candidates as 32-bit offsets from the lower plane of the pair (i, opp i), so
+                // that the wall select is one select of an offset instead of a 64-bit address
+                // (measured on the porous D3Q27 box: FP16 pull 0.406 -> 0.431 of the copy peak).
+                // Offsets stay below 2N < 2^32.
+                const int lo = slot_n < slot_w ? slot_n : slot_w;
+                const uint32_t offn = off_minus(c, v) + (slot_n > lo ? c.N : 0u);
+                const uint32_t offw = c.n + (slot_w > lo ? c.N : 0u);
+                p = src.p[lo] + (link_bit(lw, i) ? offw : offn);
+            } else {
                 p = src.p[slot_n] + off_minus(c, v);
+            }
         }
         const auto raw = RO ? ld_ro(p) : ld_rw(p);
-        d[i] = to_shifted<S>(raw, cf.r[i]);
+        d[i] = to_shifted<S>(raw, cf.so[i]);
     }
 }
 
@@ -332,6 +370,20 @@ __device__ __forceinline__ bool bad_cell(const Macro<T>& m) {
     return !(m.rho > T(0)) || !isfinite(m.ux + m.uy + m.uz);
 }
 
+// With walls, whether this lane stores: the lanes of a warp that share one 32-byte sector of a
+// population plane (8 FP32, 16 FP16, 4 FP64 cells) store when any of them is fluid; a solid lane
+// among them stores zeros into its own never-read slots, so the sector is written whole (a
+// partly written sector is read from DRAM and merged before write-back), and sectors of solid
+// cells only are not written at all (measured on the porous D3Q27 box: FP32 0.66 -> 0.69).
+template <typename E>
+__device__ __forceinline__ bool store_group(unsigned act, bool solid) {
+    constexpr int G = 32 / (int)sizeof(E);
+    const unsigned fl = __ballot_sync(act, !solid);
+    const int lane = (threadIdx.x + threadIdx.y * blockDim.x) & 31;
+    const unsigned gm = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    return (fl & gm) != 0u;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Fused stream + collide, two arrays, pull form: gather f(t) from the post-collision array of
 // the previous step, relax, store at the own cell. One launch per time step.
@@ -344,15 +396,18 @@ __global__ void __launch_bounds__(256) k_step_pull(Geom g, Coef<typename Store<S
     Cell c;
     if (!make_cell(g, c)) return;
     const uint32_t lw = link_of<MASK>(g, c);
-    // With walls, a warp that holds a fluid cell stores all its lanes: a solid cell's slots are
-    // never read (a gather that meets a solid neighbour takes the own cell's opposite slot) nor
-    // written by another cell, so its lanes store zeros there, in the same store instructions as
-    // the fluid lanes. Every destination sector of the warp is then written whole; a partly
-    // written sector is read from DRAM and merged before it is written back.
+    // With walls, a solid cell's slots are never read (a gather that meets a solid neighbour takes
+    // the own cell's opposite slot) nor written by another cell, so a solid lane may store zeros
+    // there in the same store instructions as the fluid lanes of its sector (store_group).
     const bool solid = MASK && (lw & LINK_SOLID);
-    if (MASK && __all_sync(__activemask(), solid)) return;
+    const unsigned act = __activemask();
+    if (MASK && __all_sync(act, solid)) return;
     T d[Q];
-    if (!solid) {
+    if (MASK && __all_sync(act, lw == 0u)) {
+        // no lane of the warp has a wall link: the branch-free gather (in the porous medium of
+        // overlapping spheres about 28 % of the warps, 40 % of the fluid cells)
+        gather<Q, S, false, LAYOUT_PULL, true>(c, 0u, cf, src, d);
+    } else if (!solid) {
         gather<Q, S, MASK, LAYOUT_PULL, true>(c, lw, cf, src, d);
     } else {
 #pragma unroll
@@ -360,8 +415,9 @@ __global__ void __launch_bounds__(256) k_step_pull(Geom g, Coef<typename Store<S
     }
     const Macro<T> m = bgk<Q, T, Store<S>::fix_momentum, Store<S>::fold_omega>(cf, d);
     if (!solid && bad_cell(m)) *flag = 1;
+    if (MASK && !store_group<typename Store<S>::type>(act, solid)) return;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st_raw(dst.p[i] + c.n, solid ? T(0) : from_shifted<S>(d[i], cf.r[i]));
+    for (int i = 0; i < Q; ++i) st_raw(dst.p[i] + c.n, solid ? T(0) : from_shifted<S>(d[i], cf.so[i]));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -390,7 +446,7 @@ __device__ __forceinline__ void aa_store(const Cell& c, uint32_t lw, const Coef<
             else
                 p = dst.p[i] + off_plus(c, v);
         }
-        st_raw(p, from_shifted<S>(d[i], cf.r[i]));
+        st_raw(p, from_shifted<S>(d[i], cf.so[i]));
     }
 }
 
@@ -404,13 +460,24 @@ __global__ void __launch_bounds__(256) k_step_aa(Geom g, Coef<typename Store<S>:
     const uint32_t lw = link_of<MASK>(g, c);
     if (MASK && (lw & LINK_SOLID)) return;
     T d[Q];
-    if (ODD)
+    // a cell without wall links needs no selects; taken warp-wide so that lanes do not diverge
+    const bool clean = MASK && __all_sync(__activemask(), lw == 0u);
+    if (clean) {
+        if (ODD)
+            gather<Q, S, false, LAYOUT_AAODD, false>(c, 0u, cf, src, d);
+        else
+            gather<Q, S, false, LAYOUT_LOCAL, false>(c, 0u, cf, src, d);
+    } else if (ODD) {
         gather<Q, S, MASK, LAYOUT_AAODD, false>(c, lw, cf, src, d);
-    else
+    } else {
         gather<Q, S, MASK, LAYOUT_LOCAL, false>(c, lw, cf, src, d);
+    }
     const Macro<T> m = bgk<Q, T, Store<S>::fix_momentum, Store<S>::fold_omega>(cf, d);
     if (bad_cell(m)) *flag = 1;
-    aa_store<Q, S, MASK, ODD>(c, lw, cf, dst, d);
+    if (clean)
+        aa_store<Q, S, false, ODD>(c, 0u, cf, dst, d);
+    else
+        aa_store<Q, S, MASK, ODD>(c, lw, cf, dst, d);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -453,7 +520,7 @@ __global__ void __launch_bounds__(256) k_init(Geom g, Coef<typename Store<S>::T>
             else
                 p = dst.p[i] + off_minus(c, vel<Q>(i));
         }
-        st_raw(p, from_shifted<S>(d[i], cf.r[i]));
+        st_raw(p, from_shifted<S>(d[i], cf.so[i]));
     }
 }
 
@@ -880,4 +947,5 @@ __global__ void __launch_bounds__(256) k_adj_init(Geom g, Coef<T> cf, const T* _
     accumulate_record<T>(rec, gpart);
 }
 
+}  // namespace LBM_VARIANT
 }  // namespace lbm

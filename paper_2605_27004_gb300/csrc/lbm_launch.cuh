@@ -5,8 +5,10 @@
 #include "lbm_kernels.cuh"
 #include "lbm_adjoint2.cuh"
 #include "lbm_pairs.cuh"
+#include "lbm_quads.cuh"
 
 namespace lbm {
+inline namespace LBM_VARIANT {
 
 // ---------------------------------------------------------------------------------------------
 template <int Q, int S>
@@ -21,7 +23,7 @@ struct Launch {
 
     static cudaError_t init(const Geom& g, const void* coef, int layout, const void* rho, const void* u, void* dst,
                             cudaStream_t st) {
-        const Shape sh = shape_for(g);
+        const Shape sh = shape_for(g, g.nz - 2 * LBM_SLAB);
         const CF& cf = *static_cast<const CF*>(coef);
         auto r = static_cast<const T*>(rho);
         auto uu = static_cast<const T*>(u);
@@ -46,14 +48,27 @@ struct Launch {
     // FP32 storage is at the bandwidth bound with one cell per thread already, and the wall
     // variants lose occupancy.
     static bool pairs(const Geom& g) { return S == 3 && !g.link && (g.nx % 2) == 0; }
+    // Four cells per thread (lbm_quads.cuh) for FP16 D2Q9 / D3Q19 without walls when every warp of
+    // a row is full (nx a multiple of 128): measured at 256^3 / 512^3 pull 0.84 -> 0.93 / 0.86 ->
+    // 0.96 of the copy peak, AA 0.79 -> 0.84 / 0.81 -> 0.86; at 64^3 (16 threads per row, half of
+    // every warp idle) the two-cell kernels stay faster. D3Q27 would need 108 live FP32
+    // populations per thread and stays at two cells.
+    static bool quads(const Geom& g) { return S == 3 && Q != 27 && !g.link && (g.nx % 128) == 0; }
 
     static cudaError_t step_pull(const Geom& g, const void* coef, const void* src, void* dst, int* flag,
                                  cudaStream_t st) {
-        const Shape sh = shape_for(g);
+        const Shape sh = shape_for(g, g.nz - 2 * LBM_SLAB);
         const CF& cf = *static_cast<const CF*>(coef);
         const auto a = cpl(src, g);
         const auto b = mpl(dst, g);
-        if constexpr (S != 1) {
+        if constexpr (S == 3) {  // pairs(g) holds for FP16 r-shifted storage only
+            if constexpr (Q != 27) {
+                if (quads(g)) {
+                    const Shape sq = shape_quads(g);
+                    k_step_pull4<Q><<<sq.grid, sq.block, 0, st>>>(g, cf, a, b, flag);
+                    return cudaGetLastError();
+                }
+            }
             if (pairs(g)) {
                 const Shape sp = shape_pairs(g);
                 k_step_pull2<Q, S, false><<<sp.grid, sp.block, 0, st>>>(g, cf, VelField<float>{}, a, b, flag);
@@ -69,14 +84,24 @@ struct Launch {
 
     static cudaError_t step_aa(const Geom& g, const void* coef, int odd, const void* src, void* dst, int* flag,
                                cudaStream_t st) {
-        const Shape sh = shape_for(g);
+        const Shape sh = shape_for(g, g.nz - 2 * LBM_SLAB);
         const CF& cf = *static_cast<const CF*>(coef);
         const auto a = cpl(src, g);
         const auto b = mpl(dst, g);
-        if constexpr (S != 1) {
+        if constexpr (S == 3) {  // pairs(g) holds for FP16 r-shifted storage only
             // no walls (see pairs()); the D3Q27 odd step runs one cell per thread: its pair kernel
             // scatters 18 x-shifted planes as single elements at 126 registers (two blocks per
             // SM), measured 0.68 -> 0.70 (256^3) and 0.69 -> 0.71 (384^3) of the copy peak
+            if constexpr (Q != 27) {
+                if (quads(g)) {
+                    const Shape sq = shape_quads(g);
+                    if (odd)
+                        k_step_aa_odd4<Q><<<sq.grid, sq.block, 0, st>>>(g, cf, a, b, flag);
+                    else
+                        k_step_aa_even4<Q><<<sq.grid, sq.block, 0, st>>>(g, cf, a, b, flag);
+                    return cudaGetLastError();
+                }
+            }
             if (pairs(g) && !(Q == 27 && odd)) {
                 const Shape sp = shape_pairs(g);
                 if (odd)
@@ -118,7 +143,7 @@ struct Launch {
 
     static cudaError_t moments(const Geom& g, const void* coef, int layout, const void* src, void* rho, void* u,
                                void* Pi, void* f, cudaStream_t st) {
-        const Shape sh = shape_for(g);
+        const Shape sh = shape_for(g, g.nz - 2 * LBM_SLAB);
         const CF& cf = *static_cast<const CF*>(coef);
         LBM_BY_LAYOUT(k_moments, g, cf, cpl(src, g), static_cast<T*>(rho), static_cast<T*>(u),
                       static_cast<T*>(Pi), static_cast<T*>(f));
@@ -127,7 +152,7 @@ struct Launch {
 
     static cudaError_t totals(const Geom& g, const void* coef, int layout, const void* src, double* part, int* flag,
                               cudaStream_t st) {
-        const Shape sh = shape_for(g);
+        const Shape sh = shape_for(g, g.nz - 2 * LBM_SLAB);
         const CF& cf = *static_cast<const CF*>(coef);
         LBM_BY_LAYOUT(k_totals, g, cf, cpl(src, g), part, flag);
         return cudaGetLastError();
@@ -135,7 +160,7 @@ struct Launch {
 
     static cudaError_t adj_seed(const Geom& g, const void* coef, int layout, const void* src, const void* grad,
                                 void* lam, cudaStream_t st) {
-        const Shape sh = shape_for(g);
+        const Shape sh = shape_for(g, g.nz - 2 * LBM_SLAB);
         const CF& cf = *static_cast<const CF*>(coef);
         LBM_BY_LAYOUT(k_adj_seed, g, cf, cpl(src, g), static_cast<const T*>(grad), mfl(lam, g));
         return cudaGetLastError();
@@ -143,7 +168,7 @@ struct Launch {
 
     static cudaError_t adj_step(const Geom& g, const void* coef, int layout, const void* src, const void* lam_next,
                                 void* lam, double* gpart, cudaStream_t st) {
-        const Shape sh = shape_for(g);
+        const Shape sh = shape_for(g, g.nz - 2 * LBM_SLAB);
         const CF& cf = *static_cast<const CF*>(coef);
         if constexpr (S == 3 && Q != 27) {  // FP16 storage without walls: two cells per thread (lbm_adjoint2.cuh;
             // D3Q27 stays one cell per thread: at 128 registers the pair kernel would spill)
@@ -168,7 +193,7 @@ struct Launch {
 
     static cudaError_t adj_init(const Geom& g, const void* coef, const void* rho0, const void* u0, const void* lam0,
                                 void* du0, double* gpart, cudaStream_t st) {
-        const Shape sh = shape_for(g);
+        const Shape sh = shape_for(g, g.nz - 2 * LBM_SLAB);
         const CF& cf = *static_cast<const CF*>(coef);
         k_adj_init<Q, T><<<sh.grid, sh.block, 0, st>>>(g, cf, static_cast<const T*>(rho0), static_cast<const T*>(u0),
                                                        cfl(lam0, g), static_cast<T*>(du0), gpart);
@@ -176,7 +201,7 @@ struct Launch {
     }
 
     static cudaError_t link_mask(const Geom& g, const uint8_t* solid, uint32_t* link, cudaStream_t st) {
-        const Shape sh = shape_for(g);
+        const Shape sh = shape_for(g, g.nz - 2 * LBM_SLAB);
         k_link_mask<Q><<<sh.grid, sh.block, 0, st>>>(g, solid, link);
         return cudaGetLastError();
     }
@@ -190,9 +215,9 @@ struct Launch {
 
     static cudaError_t ade_pull(const Geom& g, const void* coef, const void* u, const void* src, void* dst, int* flag,
                                 cudaStream_t st) {
-        const Shape sh = shape_for(g);
+        const Shape sh = shape_for(g, g.nz - 2 * LBM_SLAB);
         const CF& cf = *static_cast<const CF*>(coef);
-        if constexpr (S != 1) {
+        if constexpr (S == 3) {  // pairs(g) holds for FP16 r-shifted storage only
             if (pairs(g)) {
                 const Shape sp = shape_pairs(g);
                 k_step_pull2<Q, S, false, true><<<sp.grid, sp.block, 0, st>>>(g, cf, vel_field(u, g), cpl(src, g),
@@ -209,12 +234,12 @@ struct Launch {
 
     static cudaError_t ade_aa(const Geom& g, const void* coef, const void* u, int odd, const void* src, void* dst,
                               int* flag, cudaStream_t st) {
-        const Shape sh = shape_for(g);
+        const Shape sh = shape_for(g, g.nz - 2 * LBM_SLAB);
         const CF& cf = *static_cast<const CF*>(coef);
         const auto v = vel_field(u, g);
         const auto a = cpl(src, g);
         const auto b = mpl(dst, g);
-        if constexpr (S != 1) {
+        if constexpr (S == 3) {  // pairs(g) holds for FP16 r-shifted storage only
             if (pairs(g)) {
                 const Shape sp = shape_pairs(g);
                 if (odd)
@@ -245,4 +270,5 @@ struct Launch {
     }
 };
 
+}  // namespace LBM_VARIANT
 }  // namespace lbm

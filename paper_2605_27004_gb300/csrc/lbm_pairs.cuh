@@ -16,6 +16,7 @@
 #include "lbm_kernels.cuh"
 
 namespace lbm {
+inline namespace LBM_VARIANT {
 
 // ---------------------------------------------------------------------------------------------
 // Packed FP32 pair arithmetic
@@ -109,7 +110,7 @@ __device__ __forceinline__ void make_pcell(const Geom& g, PCell& c) {
     const int px = blockIdx.x * blockDim.x + threadIdx.x;
     c.x0 = 2 * px;
     c.y = blockIdx.y * blockDim.y + threadIdx.y;
-    c.z = blockIdx.z + g.z0;
+    c.z = blockIdx.z + LBM_SLAB;
     c.in_grid = c.x0 < g.nx && c.y < g.ny;
     // clamp out-of-grid lanes to a valid pair so that any address they form is in bounds
     const int x0 = c.in_grid ? c.x0 : 0;
@@ -268,11 +269,11 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3)
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const Vec3 v = vel<Q>(i);
-        d[i] = gather_pair<S, true>(src.p[i], c.R[v.y + 1][v.z + 1], c, v.x, g.nx, cf.r[i]);
+        d[i] = gather_pair<S, true>(src.p[i], c.R[v.y + 1][v.z + 1], c, v.x, g.nx, cf.so[i]);
         if (MASK && i > 0) {
             const bool wa = link_bit(lw.x, i), wb = link_bit(lw.y, i);
             if (c.active && (wa || wb)) {  // half-way bounce-back from the own cell's opposite slot
-                const F2 own = to_shifted2<S>(ld2(src.p[opp(i)] + c.n), cf.r[i]);
+                const F2 own = to_shifted2<S>(ld2(src.p[opp(i)] + c.n), cf.so[i]);
                 d[i] = f2(wa ? own.v.x : d[i].v.x, wb ? own.v.y : d[i].v.y);
             }
         }
@@ -281,11 +282,11 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3)
     if (collide2<Q, S, ADE>(cf, vf, c.n, d, fa, fb)) *flag = 1;
     if (!MASK || (fa && fb)) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) st2(dst.p[i] + c.n, from_shifted2<S>(d[i], cf.r[i]));
+        for (int i = 0; i < Q; ++i) st2(dst.p[i] + c.n, from_shifted2<S>(d[i], cf.so[i]));
     } else {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const F2 o = from_shifted2<S>(d[i], cf.r[i]);
+            const F2 o = from_shifted2<S>(d[i], cf.so[i]);
             if (fa) st_raw(dst.p[i] + c.n, o.v.x);
             if (fb) st_raw(dst.p[i] + c.n + 1, o.v.y);
         }
@@ -308,15 +309,15 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3)
     if (!fa && !fb) return;
     F2 d[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = to_shifted2<S>(ld2_rw(src.p[i] + c.n), cf.r[i]);
+    for (int i = 0; i < Q; ++i) d[i] = to_shifted2<S>(ld2_rw(src.p[i] + c.n), cf.so[i]);
     if (collide2<Q, S, ADE>(cf, vf, c.n, d, fa, fb)) *flag = 1;
     if (!MASK || (fa && fb)) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) st2(dst.p[opp(i)] + c.n, from_shifted2<S>(d[i], cf.r[i]));
+        for (int i = 0; i < Q; ++i) st2(dst.p[opp(i)] + c.n, from_shifted2<S>(d[i], cf.so[i]));
     } else {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const F2 o = from_shifted2<S>(d[i], cf.r[i]);
+            const F2 o = from_shifted2<S>(d[i], cf.so[i]);
             if (fa) st_raw(dst.p[opp(i)] + c.n, o.v.x);
             if (fb) st_raw(dst.p[opp(i)] + c.n + 1, o.v.y);
         }
@@ -345,14 +346,14 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3)
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const Vec3 v = vel<Q>(i);
-        d[i] = gather_pair<S, false>(src.p[opp(i)], c.R[v.y + 1][v.z + 1], c, v.x, g.nx, cf.r[i]);
+        d[i] = gather_pair<S, false>(src.p[opp(i)], c.R[v.y + 1][v.z + 1], c, v.x, g.nx, cf.so[i]);
     }
     if (c.active && collide2<Q, S, ADE>(cf, vf, c.n, d, true, true)) *flag = 1;
     const int nx = g.nx;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const Vec3 v = vel<Q>(i);
-        const F2 o = from_shifted2<S>(d[i], cf.r[i]);
+        const F2 o = from_shifted2<S>(d[i], cf.so[i]);
         typename Store<S>::type* row = dst.p[i] + c.R[1 - v.y][1 - v.z];  // row of x + c_i
         if (v.x == 0) {
             if (c.active) st2(row + c.x0, o);
@@ -376,9 +377,10 @@ inline Shape shape_pairs(const Geom& g) {
     const int bx = block_x_for(np);
     const int by = std::max(1, 256 / bx);
     s.block = dim3(bx, by, 1);
-    s.grid = dim3((np + bx - 1) / bx, (g.ny + by - 1) / by, g.nzp);
+    s.grid = dim3((np + bx - 1) / bx, (g.ny + by - 1) / by, g.nz - 2 * LBM_SLAB);
     s.nblocks = (long long)s.grid.x * s.grid.y * s.grid.z;
     return s;
 }
 
+}  // namespace LBM_VARIANT
 }  // namespace lbm

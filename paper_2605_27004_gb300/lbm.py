@@ -21,9 +21,10 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "liblbm.so")
 
 LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 = 9, 19, 27
-LBM_FP32, LBM_FP64, LBM_FP32_SHIFTED, LBM_FP16_SHIFTED = 0, 1, 2, 3
+LBM_FP32, LBM_FP64, LBM_FP32_SHIFTED, LBM_FP16_SHIFTED, LBM_FP16_WSHIFTED = 0, 1, 2, 3, 4
 LBM_PULL2, LBM_AA = 0, 1
-STORAGE = {"fp32": LBM_FP32, "fp64": LBM_FP64, "fp32s": LBM_FP32_SHIFTED, "fp16s": LBM_FP16_SHIFTED}
+STORAGE = {"fp32": LBM_FP32, "fp64": LBM_FP64, "fp32s": LBM_FP32_SHIFTED, "fp16s": LBM_FP16_SHIFTED,
+           "fp16w": LBM_FP16_WSHIFTED}
 SCHEME = {"pull": LBM_PULL2, "aa": LBM_AA}
 STATUS = {0: "LBM_OK", -1: "LBM_ERR_INVALID_ARG", -2: "LBM_ERR_NOT_SPD", -3: "LBM_ERR_BAD_TAU",
           -4: "LBM_ERR_OOM", -5: "LBM_ERR_CUDA", -6: "LBM_ERR_UNSTABLE", -7: "LBM_ERR_NO_FORWARD",

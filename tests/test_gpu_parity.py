@@ -194,15 +194,17 @@ def test_error_paths():
     assert e.value.status == -6
 
 
-# Geometries for the two-cells-per-thread kernels (FP16 storage, even nx): rows shorter than a
-# warp, rows of one and several warps (nx = 64, 128, 256, 384: the x wrap crosses a warp or a
-# block boundary), odd nx (one-cell fallback), ragged ny and nz = 1
+# Geometries for the two- and four-cells-per-thread kernels (FP16 storage; even nx two cells,
+# nx a multiple of 128 four cells): rows shorter than a warp, rows of one and several warps
+# (nx = 64, 128, 256, 384: the x wrap crosses a warp or a block boundary), odd nx (one-cell
+# fallback), ragged ny and nz = 1
 PAIR_GEOMS = [(19, (2, 5, 4)), (19, (64, 3, 3)), (19, (130, 3, 2)), (19, (46, 13, 9)), (27, (38, 11, 10)),
-              (9, (98, 21, 1)), (19, (45, 7, 6)), (19, (128, 7, 5)), (27, (256, 5, 3)), (9, (384, 9, 1))]
+              (9, (98, 21, 1)), (19, (45, 7, 6)), (19, (128, 7, 5)), (27, (256, 5, 3)), (9, (384, 9, 1)),
+              (19, (256, 3, 4))]
 
 
 @pytest.mark.parametrize("q,dims", PAIR_GEOMS)
-@pytest.mark.parametrize("storage", ["fp32s", "fp32", "fp16s"])
+@pytest.mark.parametrize("storage", ["fp32s", "fp32", "fp16s", "fp16w"])
 @pytest.mark.parametrize("scheme", ["pull", "aa"])
 @pytest.mark.parametrize("mask", [None, "random"])
 def test_fp32_and_fp16_kernels_match_oracle(q, dims, storage, scheme, mask):
@@ -219,8 +221,11 @@ def test_fp32_and_fp16_kernels_match_oracle(q, dims, storage, scheme, mask):
     g = gpu_run(q, dims, 0.7, Th, rho0, u0, 40, solid=solid, storage=storage, scheme=scheme)
     o = oracle_run(q, dims, 0.7, Th, rho0, u0, 40, solid=solid)
     fl = slice(None) if solid is None else (solid == 0)
-    tol = {"fp16s": 1e-3, "fp32": 2e-5, "fp32s": 2e-6}[storage]
+    # fp16w (FP16 of f - w rho0, the comparison form for the r_i shift) rounds stored values that
+    # carry r_i - w_i rho0 ~ 0.1 w_i at these Theta: measured 3.7e-3 after 40 steps
+    tol = {"fp16s": 1e-3, "fp16w": 2e-2, "fp32": 2e-5, "fp32s": 2e-6}[storage]
     assert rel_l2(g["u"][:, fl], o["u"][:, fl]) < tol
     perm = perm_lib_to_oracle(q)
     f_or = o["f"][:, perm].T
-    assert np.abs(g["f"] - f_or).max() < (2e-3 if storage == "fp16s" else 2e-6) * np.abs(f_or).max()
+    ftol = {"fp16s": 2e-3, "fp16w": 1e-2}.get(storage, 2e-6)
+    assert np.abs(g["f"] - f_or).max() < ftol * np.abs(f_or).max()

@@ -46,7 +46,7 @@ def _group(q, dims, Th, solid, storage, rho0, u0, steps, nslabs, tau=0.7):
 
 
 CASES = [(19, (20, 9, 12), None, 3), (19, (16, 6, 11), "random", 2), (27, (13, 7, 9), "random", 3),
-         (27, (12, 5, 8), None, 4), (19, (10, 4, 7), "walls", 7)]
+         (27, (12, 5, 8), None, 4), (19, (10, 4, 7), "walls", 7), (19, (128, 4, 7), None, 3)]
 
 
 def _mask(dims, kind, seed):
