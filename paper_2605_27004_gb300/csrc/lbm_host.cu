@@ -134,6 +134,8 @@ struct lbm_ctx {
     Shape shape{};
     uint32_t* link = nullptr;  // per-cell link words (N), null for an all-fluid box
     long long n_fluid = 0;
+    uint32_t* cell_idx = nullptr;  // fluid-cell list of FP16 contexts with walls (n_fluid entries)
+    CellList cells{};
 
     Coef<double> cd{};
     Coef<float> cf{};
@@ -333,6 +335,15 @@ void drop_graph(lbm_ctx* c) {
     c->graph_steps = 0;
 }
 
+// One forward step src -> dst of a flow context on stream s (t = steps done before it): over the
+// fluid-cell list when the context has one (FP16 AA with walls), else over the grid.
+cudaError_t step_kernel(lbm_ctx* c, const void* src, void* dst, long long t, cudaStream_t s) {
+    if (c->cell_idx)  // AA scheme only
+        return c->ops->step_aa_list(c->geom, c->coef(), c->cells, (int)(t & 1), src, dst, c->flag, s);
+    return c->scheme == LBM_PULL2 ? c->ops->step_pull(c->geom, c->coef(), src, dst, c->flag, s)
+                                  : c->ops->step_aa(c->geom, c->coef(), (int)(t & 1), src, dst, c->flag, s);
+}
+
 int layout_now(const lbm_ctx* c, long long steps) {
     if (c->scheme == LBM_PULL2) return LAYOUT_PULL;
     return (steps & 1) ? LAYOUT_AAODD : LAYOUT_LOCAL;
@@ -352,10 +363,10 @@ cudaError_t launch_step(lbm_ctx* c, cudaStream_t s) {
             e = c->ops->ade_aa(c->geom, c->coef(), u, (int)(c->steps & 1), c->pop[0], c->pop[0], c->flag, s);
         }
     } else if (c->scheme == LBM_PULL2) {
-        e = c->ops->step_pull(c->geom, c->coef(), c->pop[c->cur], c->pop[c->cur ^ 1], c->flag, s);
+        e = step_kernel(c, c->pop[c->cur], c->pop[c->cur ^ 1], c->steps, s);
         c->cur ^= 1;
     } else {
-        e = c->ops->step_aa(c->geom, c->coef(), (int)(c->steps & 1), c->pop[0], c->pop[0], c->flag, s);
+        e = step_kernel(c, c->pop[0], c->pop[0], c->steps, s);
     }
     c->steps += 1;
     c->launches += 1;
@@ -577,6 +588,7 @@ void lbm_destroy(lbm_ctx* c) {
     dev_free(c, c->pop[0], SB);
     dev_free(c, c->pop[1], SB);
     dev_free(c, c->link, (size_t)c->N * 4);
+    dev_free(c, c->cell_idx, (size_t)c->cells.count * 4 + 4);
     for (size_t k = 0; k < c->rec_ptr.size(); ++k) {
         if (!c->rec_ptr[k]) continue;
         if (c->rec_host[k])
@@ -699,6 +711,24 @@ int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau
             dev_free(c, dmask, (size_t)c->N);
             if (e != cudaSuccess) return bail(cuda_fail(c, e, "link-mask construction"));
             c->geom.link = c->link;
+            // FP16 storage is limited by issued instructions: for the AA scheme list the fluid cells
+            // (interior planes only) so that no lane of a warp belongs to a solid cell
+            if ((c->storage == LBM_FP16_SHIFTED || c->storage == LBM_FP16_WSHIFTED) && c->scheme == LBM_AA &&
+                nx >= 2) {
+                std::vector<uint32_t> idx;
+                idx.reserve((size_t)c->n_fluid);
+                const long long z0 = c->slab ? 1 : 0;
+                for (long long n = z0 * plane; n < (z0 + nz) * plane; ++n)
+                    if (!m[(size_t)n]) idx.push_back((uint32_t)n);
+                c->cell_idx = (uint32_t*)dev_alloc(c, idx.size() * 4 + 4);
+                if (!c->cell_idx) return bail(fail(c, LBM_ERR_OOM, "fluid-cell list"));
+                e = cudaMemcpy(c->cell_idx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) return bail(cuda_fail(c, e, "fluid-cell list upload"));
+                c->cells.idx = c->cell_idx;
+                c->cells.count = (uint32_t)idx.size();
+                c->cells.rnx = ~0ULL / (unsigned long long)nx + 1ULL;
+                c->cells.rnxy = ~0ULL / (unsigned long long)plane + 1ULL;
+            }
         }
     }
     const size_t SB = c->state_bytes();
@@ -973,9 +1003,7 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
     // one forward step src -> dst (then the ghost planes of dst, for a z-slab)
     auto step_oop = [&](const void* src, void* dst, long long t, const char* what) -> int {
         c->launches += 1;
-        const cudaError_t e = c->scheme == LBM_PULL2
-                                  ? c->ops->step_pull(c->geom, cf, src, dst, c->flag, c->stream)
-                                  : c->ops->step_aa(c->geom, cf, (int)(t & 1), src, dst, c->flag, c->stream);
+        const cudaError_t e = step_kernel(c, src, dst, t, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, what);
         return run_halo(c, LBM_HALO_POPULATIONS, dst);
     };
@@ -1109,11 +1137,7 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
         if (!c->cap_stream) LBM_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
         LBM_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;
-        for (int j = 1; j < K && e == cudaSuccess; ++j)
-            e = c->scheme == LBM_PULL2
-                    ? c->ops->step_pull(c->geom, cf, bufs[j - 1], bufs[j], c->flag, c->cap_stream)
-                    : c->ops->step_aa(c->geom, cf, (int)((t0 + j - 1) & 1), bufs[j - 1], bufs[j], c->flag,
-                                      c->cap_stream);
+        for (int j = 1; j < K && e == cudaSuccess; ++j) e = step_kernel(c, bufs[j - 1], bufs[j], t0 + j - 1, c->cap_stream);
         int l = lc;
         for (int j = K - 1; j >= 0 && e == cudaSuccess; --j) {
             e = c->ops->adj_step(c->geom, cf, layout_now(c, t0 + j), bufs[j], c->lam[l], c->lam[l ^ 1], c->gpart,
@@ -1375,7 +1399,14 @@ int lbm_ade_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, double ta
         return LBM_ERR_INVALID_ARG;
     }
     const int rc = lbm_create_ex(out, lattice, nx, ny, nz, tau, Theta, solid_mask, opt);
-    if (rc == LBM_OK) (*out)->kind = 1;
+    if (rc == LBM_OK) {
+        lbm_ctx* c = *out;
+        c->kind = 1;
+        // the scalar's step kernels run over the grid: no fluid-cell list
+        dev_free(c, c->cell_idx, (size_t)c->cells.count * 4 + 4);
+        c->cell_idx = nullptr;
+        c->cells = CellList{};
+    }
     return rc;
 }
 

@@ -65,7 +65,7 @@ struct Launch {
             if constexpr (Q != 27) {
                 if (quads(g)) {
                     const Shape sq = shape_quads(g);
-                    k_step_pull4<Q><<<sq.grid, sq.block, 0, st>>>(g, cf, a, b, flag);
+                    k_step_pull4<Q><<<sq.grid, sq.block, 0, st>>>(g, cf, VelField<float>{}, a, b, flag);
                     return cudaGetLastError();
                 }
             }
@@ -96,9 +96,9 @@ struct Launch {
                 if (quads(g)) {
                     const Shape sq = shape_quads(g);
                     if (odd)
-                        k_step_aa_odd4<Q><<<sq.grid, sq.block, 0, st>>>(g, cf, a, b, flag);
+                        k_step_aa_odd4<Q><<<sq.grid, sq.block, 0, st>>>(g, cf, VelField<float>{}, a, b, flag);
                     else
-                        k_step_aa_even4<Q><<<sq.grid, sq.block, 0, st>>>(g, cf, a, b, flag);
+                        k_step_aa_even4<Q><<<sq.grid, sq.block, 0, st>>>(g, cf, VelField<float>{}, a, b, flag);
                     return cudaGetLastError();
                 }
             }
@@ -122,6 +122,18 @@ struct Launch {
             else
                 k_step_aa<Q, S, false, 0><<<sh.grid, sh.block, 0, st>>>(g, cf, a, b, flag);
         }
+        return cudaGetLastError();
+    }
+
+    static cudaError_t step_aa_list(const Geom& g, const void* coef, const CellList& L, int odd, const void* src,
+                                    void* dst, int* flag, cudaStream_t st) {
+        if (L.count == 0) return cudaSuccess;
+        const CF& cf = *static_cast<const CF*>(coef);
+        const unsigned nb = (L.count + 255) / 256;
+        if (odd)
+            k_step_aa_list<Q, S, 1><<<nb, 256, 0, st>>>(g, cf, L, cpl(src, g), mpl(dst, g), flag);
+        else
+            k_step_aa_list<Q, S, 0><<<nb, 256, 0, st>>>(g, cf, L, cpl(src, g), mpl(dst, g), flag);
         return cudaGetLastError();
     }
 
@@ -218,6 +230,14 @@ struct Launch {
         const Shape sh = shape_for(g, g.nz - 2 * LBM_SLAB);
         const CF& cf = *static_cast<const CF*>(coef);
         if constexpr (S == 3) {  // pairs(g) holds for FP16 r-shifted storage only
+            if constexpr (Q != 27) {
+                if (quads(g)) {
+                    const Shape sq = shape_quads(g);
+                    k_step_pull4<Q, true><<<sq.grid, sq.block, 0, st>>>(g, cf, vel_field(u, g), cpl(src, g),
+                                                                       mpl(dst, g), flag);
+                    return cudaGetLastError();
+                }
+            }
             if (pairs(g)) {
                 const Shape sp = shape_pairs(g);
                 k_step_pull2<Q, S, false, true><<<sp.grid, sp.block, 0, st>>>(g, cf, vel_field(u, g), cpl(src, g),
@@ -240,6 +260,16 @@ struct Launch {
         const auto a = cpl(src, g);
         const auto b = mpl(dst, g);
         if constexpr (S == 3) {  // pairs(g) holds for FP16 r-shifted storage only
+            if constexpr (Q != 27) {
+                if (quads(g)) {
+                    const Shape sq = shape_quads(g);
+                    if (odd)
+                        k_step_aa_odd4<Q, true><<<sq.grid, sq.block, 0, st>>>(g, cf, v, a, b, flag);
+                    else
+                        k_step_aa_even4<Q, true><<<sq.grid, sq.block, 0, st>>>(g, cf, v, a, b, flag);
+                    return cudaGetLastError();
+                }
+            }
             if (pairs(g)) {
                 const Shape sp = shape_pairs(g);
                 if (odd)
@@ -264,8 +294,8 @@ struct Launch {
     }
 
     static const Ops& ops() {
-        static const Ops o = {&init, &step_pull, &step_aa, &moments, &totals, &adj_seed, &adj_step, &adj_init,
-                              &link_mask, &ade_pull, &ade_aa};
+        static const Ops o = {&init,     &step_pull, &step_aa,   &step_aa_list, &moments, &totals, &adj_seed,
+                              &adj_step, &adj_init,  &link_mask, &ade_pull,     &ade_aa};
         return o;
     }
 };

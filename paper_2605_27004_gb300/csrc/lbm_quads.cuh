@@ -9,8 +9,9 @@
 // the even AA step are one aligned 8-byte word per plane; the odd AA step scatters along +c_i and
 // writes the x-shifted planes as one aligned 4-byte word plus two halves. Per cell this halves
 // the load, store, address and conversion instructions of the two-cells-per-thread kernels, which
-// are instruction-bound for FP16 storage. The collision is the packed pair collision (bgk2) on
-// (x0, x0 + 1) and then on (x0 + 2, x0 + 3).
+// are instruction-bound for FP16 storage. The collision is the packed pair collision (collide2:
+// the flow's BGK, or with ADE the scalar's relaxation with the prescribed velocity read as aligned
+// float2 pairs) on (x0, x0 + 1) and then on (x0 + 2, x0 + 3).
 #pragma once
 #include "lbm_pairs.cuh"
 
@@ -94,9 +95,9 @@ __device__ __forceinline__ void st_word4(__half* p, F2 a, F2 b) {
 // ---------------------------------------------------------------------------------------------
 // Pull step, four cells per thread (FP16 r-shifted storage: the stored value is d = f - r).
 // ---------------------------------------------------------------------------------------------
-template <int Q>
+template <int Q, bool ADE = false>
 __global__ void __launch_bounds__(256, 2)
-    k_step_pull4(Geom g, Coef<float> cf, const Planes<const __half> src, const Planes<__half> dst,
+    k_step_pull4(Geom g, Coef<float> cf, VelField<float> vf, const Planes<const __half> src, const Planes<__half> dst,
                  int* __restrict__ flag) {
     QCell c;
     make_qcell(g, c);
@@ -107,8 +108,7 @@ __global__ void __launch_bounds__(256, 2)
         gather_quad<true>(src.p[i], c.R[v.y + 1][v.z + 1], c, v.x, g.nx, da[i], db[i]);
     }
     if (!c.active) return;
-    const bool bad = collide2<Q, 3, false>(cf, VelField<float>{}, c.n, da, true, true) |
-                     collide2<Q, 3, false>(cf, VelField<float>{}, c.n + 2, db, true, true);
+    const bool bad = collide2<Q, 3, ADE>(cf, vf, c.n, da, true, true) | collide2<Q, 3, ADE>(cf, vf, c.n + 2, db, true, true);
     if (bad) *flag = 1;
 #pragma unroll
     for (int i = 0; i < Q; ++i) st_word4(dst.p[i] + c.n, da[i], db[i]);
@@ -117,9 +117,9 @@ __global__ void __launch_bounds__(256, 2)
 // ---------------------------------------------------------------------------------------------
 // AA even step (state LOCAL -> AAODD), four cells per thread: purely local, aligned words.
 // ---------------------------------------------------------------------------------------------
-template <int Q>
+template <int Q, bool ADE = false>
 __global__ void __launch_bounds__(256, 2)
-    k_step_aa_even4(Geom g, Coef<float> cf, const Planes<const __half> src, const Planes<__half> dst,
+    k_step_aa_even4(Geom g, Coef<float> cf, VelField<float> vf, const Planes<const __half> src, const Planes<__half> dst,
                     int* __restrict__ flag) {
     QCell c;
     make_qcell(g, c);
@@ -131,8 +131,7 @@ __global__ void __launch_bounds__(256, 2)
         da[i] = half2_bits_to_f2(w.x);
         db[i] = half2_bits_to_f2(w.y);
     }
-    const bool bad = collide2<Q, 3, false>(cf, VelField<float>{}, c.n, da, true, true) |
-                     collide2<Q, 3, false>(cf, VelField<float>{}, c.n + 2, db, true, true);
+    const bool bad = collide2<Q, 3, ADE>(cf, vf, c.n, da, true, true) | collide2<Q, 3, ADE>(cf, vf, c.n + 2, db, true, true);
     if (bad) *flag = 1;
 #pragma unroll
     for (int i = 0; i < Q; ++i) st_word4(dst.p[opp(i)] + c.n, da[i], db[i]);
@@ -147,9 +146,9 @@ __global__ void __launch_bounds__(256, 2)
 // place and race free; elements of the neighbouring words that a thread loads but does not own
 // are never used by it.
 // ---------------------------------------------------------------------------------------------
-template <int Q>
+template <int Q, bool ADE = false>
 __global__ void __launch_bounds__(256, 2)
-    k_step_aa_odd4(Geom g, Coef<float> cf, const Planes<const __half> src, const Planes<__half> dst,
+    k_step_aa_odd4(Geom g, Coef<float> cf, VelField<float> vf, const Planes<const __half> src, const Planes<__half> dst,
                    int* __restrict__ flag) {
     QCell c;
     make_qcell(g, c);
@@ -160,8 +159,7 @@ __global__ void __launch_bounds__(256, 2)
         gather_quad<false>(src.p[opp(i)], c.R[v.y + 1][v.z + 1], c, v.x, g.nx, da[i], db[i]);
     }
     if (!c.active) return;
-    const bool bad = collide2<Q, 3, false>(cf, VelField<float>{}, c.n, da, true, true) |
-                     collide2<Q, 3, false>(cf, VelField<float>{}, c.n + 2, db, true, true);
+    const bool bad = collide2<Q, 3, ADE>(cf, vf, c.n, da, true, true) | collide2<Q, 3, ADE>(cf, vf, c.n + 2, db, true, true);
     if (bad) *flag = 1;
     const int nx = g.nx;
 #pragma unroll
