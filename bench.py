@@ -14,6 +14,8 @@ Modes
   --mode sweep     one JSON line per variant (lattice x storage x scheme x size, porous runs).
   --mode profile   a small case of one kernel for ncu (--lattice/--storage/--scheme/--n/--kernel).
   --mode slabs     the z-slab decomposition on one GPU against the whole box (--n, --storage).
+  --sharded        the contract line for one box cut into z-slabs over the ranks (strong scaling,
+                   halo exchange over torch.distributed) instead of independent replicas.
   --impl reference the oracle itself timed on the host cores (the reference arm).
 """
 from __future__ import annotations
@@ -488,6 +490,50 @@ def run_slabs(args, torch, lbm):
           flush=True)
 
 
+def run_sharded(args, torch, lbm, dist, world, rank, local):
+    """Strong scaling of the z-slab decomposition: one n^3 D3Q19 Taylor-Green box (default 512^3,
+    shifted FP32) cut into `world` slabs, one per rank, the halo planes exchanged over
+    torch.distributed (NCCL) after every step. value = cells of the whole box x steps / the
+    slowest rank's time. With one rank the slab exchanges with itself through the same code."""
+    from paper_2605_27004_gb300 import slabs
+    peak, peak_src = measured_peak()
+    n = args.n if args.n != 128 else 512
+    dims, tau, Th, rho0, u0, _ = problem(19, n, "tg")
+    N = int(np.prod(dims))
+    D = slabs.DistributedSlab(19, *dims, tau, Th, storage="fp32s")
+    u0t = u0 if isinstance(u0, torch.Tensor) else torch.as_tensor(u0, dtype=torch.float32)
+    r0 = None if rho0 is None else slabs.slab_of(torch.as_tensor(rho0, dtype=torch.float32).cuda(), D.plan, *dims[:2])
+    D.L.init(r0, slabs.slab_of(u0t.cuda().reshape(3, -1), D.plan, *dims[:2]))
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms, kms, launches = time_steps(D.L, args.steps, args.warmup, torch)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    D.L.close()
+    ms_max, _ = job_throughput(ms, 1, 1, dist, torch)
+    if rank != 0:
+        return
+    nloc = dims[0] * dims[1] * D.plan.nz_local
+    line = {
+        "metric": "MLUPS", "value": N * args.steps / (ms_max * 1e-3) / 1e6, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "D3Q19 FP32 %d^3 periodic Taylor-Green, u0 0.02, rotated Theta, tau 0.6, shifted "
+                               "FP32 storage, cut into %d z-slabs" % (n, world),
+                   "cells": N, "parallelism": "z-slabs, halo planes over torch.distributed after every step",
+                   "l2": "inputs larger than L2"},
+        "roofline": {"bound": "hbm", "achieved": 152 * nloc / (kms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": 152 * nloc / (kms * 1e-3) / 1e9 / peak, "traffic": None, "peak_source": peak_src,
+                     "kernel": "k_step_pull<19, FP32_SHIFTED> (slab objects) + halo exchange, rank 0",
+                     "note": "per-step event time includes the halo pack, exchange and unpack"},
+        "cpu_baseline": None, "e2e": None, "clocks": clk.summary(), "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_profile(args, torch, lbm):
     """Small case for ncu: --kernel fwd runs warmup + steps forward launches; --kernel adjoint
     runs one short adjoint (seed, recompute, adjoint steps)."""
@@ -521,6 +567,8 @@ def main():
     ap.add_argument("--kernel", default="fwd", choices=["fwd", "adjoint"])
     ap.add_argument("--porous", action="store_true")
     ap.add_argument("--ade", action="store_true", help="profile: the scalar advection-diffusion workload")
+    ap.add_argument("--sharded", action="store_true",
+                    help="one box cut into z-slabs over the ranks (strong scaling) instead of replicas")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -553,6 +601,12 @@ def main():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
+
+    if args.sharded:
+        run_sharded(args, torch, lbm, dist, world, rank, local)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     peak, peak_src = measured_peak()
     q, n, storage = 19, 256, "fp32s"
