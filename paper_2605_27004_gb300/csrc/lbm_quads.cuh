@@ -7,7 +7,8 @@
 // comes from, from which the shifted window of four halves is cut with two byte permutations (the
 // neighbouring word is the adjacent lane's, so the second load hits L1). Stores of the pull and
 // the even AA step are one aligned 8-byte word per plane; the odd AA step scatters along +c_i and
-// writes the x-shifted planes as one aligned 4-byte word plus two halves. Per cell this halves
+// completes each thread's aligned word of an x-shifted plane with one value from the neighbouring
+// lane (warp shuffle). Per cell this halves
 // the load, store, address and conversion instructions of the two-cells-per-thread kernels, which
 // are instruction-bound for FP16 storage. The collision is the packed pair collision (collide2:
 // the flow's BGK, or with ADE the scalar's relaxation with the prescribed velocity read as aligned
@@ -162,22 +163,50 @@ __global__ void __launch_bounds__(256, 2)
     const bool bad = collide2<Q, 3, ADE>(cf, vf, c.n, da, true, true) | collide2<Q, 3, ADE>(cf, vf, c.n + 2, db, true, true);
     if (bad) *flag = 1;
     const int nx = g.nx;
+    // Rows are multiples of 128 cells (quads()), so a warp is 32 threads of one row, its lane 0 the
+    // row start or the successor of another warp's lane 31. For c_x = +-1 the value that belongs to
+    // the thread's own aligned word but comes from the neighbouring lane's cell is taken by a warp
+    // shuffle, and the word is stored whole; only the warp's end lanes store single halves across
+    // the warp boundary. Each slot is still written after the lane that gathered it has gathered it:
+    // the shuffled value depends on that lane's gather (measured for the flow at 256^3 / 512^3 /
+    // 768^3: AA 0.843 -> 0.854 / 0.864 -> 0.888 / 0.874 -> 0.867).
+    const int lane = (threadIdx.x + threadIdx.y * blockDim.x) & 31;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const Vec3 v = vel<Q>(i);
         __half* row = dst.p[i] + c.R[1 - v.y][1 - v.z];  // row of x + c_i
         if (v.x == 0) {
             st_word4(row + c.x0, da[i], db[i]);
-        } else {
-            const unsigned wa = f2_to_half2_bits(da[i]), wb = f2_to_half2_bits(db[i]);
-            const unsigned short lo = (unsigned short)(wa & 0xffffu), hi = (unsigned short)(wb >> 16);
-            // targets x0 + c_x .. x0 + 3 + c_x: the first half, the aligned middle pair, the last half
+            continue;
+        }
+        const unsigned wa = f2_to_half2_bits(da[i]), wb = f2_to_half2_bits(db[i]);
+        if constexpr (ADE) {  // the scalar keeps the three stores per plane (measured 0.851 -> 0.833 with shuffles)
             const int xf = v.x == 1 ? c.x0 + 1 : (c.x0 == 0 ? nx - 1 : c.x0 - 1);
             const int xm = v.x == 1 ? c.x0 + 2 : c.x0;
             const int xl = v.x == 1 ? (c.x0 + 4 == nx ? 0 : c.x0 + 4) : c.x0 + 2;
-            *reinterpret_cast<unsigned short*>(row + xf) = lo;
+            *reinterpret_cast<unsigned short*>(row + xf) = (unsigned short)(wa & 0xffffu);
             *reinterpret_cast<unsigned*>(row + xm) = mid_halves(wa, wb);
-            *reinterpret_cast<unsigned short*>(row + xl) = hi;
+            *reinterpret_cast<unsigned short*>(row + xl) = (unsigned short)(wb >> 16);
+        } else if (v.x == 1) {  // targets x0 + 1 .. x0 + 4: own word gets (lane - 1's last, a.x, a.y, b.x)
+            const unsigned prev = __shfl_up_sync(0xffffffffu, wb >> 16, 1);
+            if (lane != 0) {
+                *reinterpret_cast<uint2*>(row + c.x0) = make_uint2((prev & 0xffffu) | (wa << 16), mid_halves(wa, wb));
+            } else {
+                *reinterpret_cast<unsigned short*>(row + c.x0 + 1) = (unsigned short)(wa & 0xffffu);
+                *reinterpret_cast<unsigned*>(row + c.x0 + 2) = mid_halves(wa, wb);
+            }
+            if (lane == 31)  // into the next warp's word (or the row start)
+                *reinterpret_cast<unsigned short*>(row + (c.x0 + 4 == nx ? 0 : c.x0 + 4)) = (unsigned short)(wb >> 16);
+        } else {  // targets x0 - 1 .. x0 + 2: own word gets (a.y, b.x, b.y, lane + 1's first)
+            const unsigned next = __shfl_down_sync(0xffffffffu, wa & 0xffffu, 1);
+            if (lane != 31) {
+                *reinterpret_cast<uint2*>(row + c.x0) = make_uint2(mid_halves(wa, wb), (wb >> 16) | (next << 16));
+            } else {
+                *reinterpret_cast<unsigned*>(row + c.x0) = mid_halves(wa, wb);
+                *reinterpret_cast<unsigned short*>(row + c.x0 + 2) = (unsigned short)(wb >> 16);
+            }
+            if (lane == 0)  // into the previous warp's word (or the row end)
+                *reinterpret_cast<unsigned short*>(row + (c.x0 == 0 ? nx - 1 : c.x0 - 1)) = (unsigned short)(wa & 0xffffu);
         }
     }
 }
