@@ -134,7 +134,7 @@ struct lbm_ctx {
     Shape shape{};
     uint32_t* link = nullptr;  // per-cell link words (N), null for an all-fluid box
     long long n_fluid = 0;
-    uint32_t* cell_idx = nullptr;  // fluid-cell list of FP16 contexts with walls (n_fluid entries)
+    uint32_t* cell_idx = nullptr;  // FP16 with walls: fluid cells (AA) or 16-cell sectors (pull)
     CellList cells{};
 
     Coef<double> cd{};
@@ -336,10 +336,12 @@ void drop_graph(lbm_ctx* c) {
 }
 
 // One forward step src -> dst of a flow context on stream s (t = steps done before it): over the
-// fluid-cell list when the context has one (FP16 AA with walls), else over the grid.
+// lists of an FP16 context with walls (sectors for pull, cells for AA), else over the grid.
 cudaError_t step_kernel(lbm_ctx* c, const void* src, void* dst, long long t, cudaStream_t s) {
-    if (c->cell_idx)  // AA scheme only
-        return c->ops->step_aa_list(c->geom, c->coef(), c->cells, (int)(t & 1), src, dst, c->flag, s);
+    if (c->cell_idx)
+        return c->scheme == LBM_PULL2
+                   ? c->ops->step_pull_sectors(c->geom, c->coef(), c->cells, src, dst, c->flag, s)
+                   : c->ops->step_aa_list(c->geom, c->coef(), c->cells, (int)(t & 1), src, dst, c->flag, s);
     return c->scheme == LBM_PULL2 ? c->ops->step_pull(c->geom, c->coef(), src, dst, c->flag, s)
                                   : c->ops->step_aa(c->geom, c->coef(), (int)(t & 1), src, dst, c->flag, s);
 }
@@ -711,15 +713,25 @@ int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau
             dev_free(c, dmask, (size_t)c->N);
             if (e != cudaSuccess) return bail(cuda_fail(c, e, "link-mask construction"));
             c->geom.link = c->link;
-            // FP16 storage is limited by issued instructions: for the AA scheme list the fluid cells
-            // (interior planes only) so that no lane of a warp belongs to a solid cell
-            if ((c->storage == LBM_FP16_SHIFTED || c->storage == LBM_FP16_WSHIFTED) && c->scheme == LBM_AA &&
-                nx >= 2) {
+            // FP16 storage is limited by issued instructions: list the fluid cells (AA: no lane of a
+            // warp belongs to a solid cell) or the 16-cell sectors that hold one (pull: the stores
+            // stay whole sectors), over the interior planes only
+            if ((c->storage == LBM_FP16_SHIFTED || c->storage == LBM_FP16_WSHIFTED) && nx >= 2) {
                 std::vector<uint32_t> idx;
-                idx.reserve((size_t)c->n_fluid);
                 const long long z0 = c->slab ? 1 : 0;
-                for (long long n = z0 * plane; n < (z0 + nz) * plane; ++n)
-                    if (!m[(size_t)n]) idx.push_back((uint32_t)n);
+                const long long nb = z0 * plane, ne = (z0 + nz) * plane;
+                if (c->scheme == LBM_AA) {
+                    idx.reserve((size_t)c->n_fluid);
+                    for (long long n = nb; n < ne; ++n)
+                        if (!m[(size_t)n]) idx.push_back((uint32_t)n);
+                } else {
+                    for (long long s0 = nb / 16; s0 * 16 < ne; ++s0) {
+                        bool any = false;
+                        for (long long n = std::max(s0 * 16, nb); n < std::min(s0 * 16 + 16, ne) && !any; ++n)
+                            any = !m[(size_t)n];
+                        if (any) idx.push_back((uint32_t)s0);
+                    }
+                }
                 c->cell_idx = (uint32_t*)dev_alloc(c, idx.size() * 4 + 4);
                 if (!c->cell_idx) return bail(fail(c, LBM_ERR_OOM, "fluid-cell list"));
                 e = cudaMemcpy(c->cell_idx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice);
@@ -728,6 +740,8 @@ int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau
                 c->cells.count = (uint32_t)idx.size();
                 c->cells.rnx = ~0ULL / (unsigned long long)nx + 1ULL;
                 c->cells.rnxy = ~0ULL / (unsigned long long)plane + 1ULL;
+                c->cells.n_begin = (uint32_t)nb;
+                c->cells.n_end = (uint32_t)ne;
             }
         }
     }

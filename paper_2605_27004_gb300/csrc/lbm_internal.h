@@ -22,7 +22,8 @@ struct Geom {
 constexpr uint32_t LINK_SOLID = 0x80000000u;
 
 // The fluid cells of a box with walls, listed in increasing cell index, so that a kernel can give
-// every lane of a warp a fluid cell (FP16 AA steps) (rows of the porous medium are about 30 % solid, and a lane
+// every lane of a warp a fluid cell (FP16 AA steps); or, for the FP16 pull step, the 16-cell
+// groups (one 32-byte sector of every FP16 plane) that hold at least one fluid cell (rows of the porous medium are about 30 % solid, and a lane
 // of a solid cell still issues every instruction of its warp). A cell's coordinates come back
 // from its index by exact reciprocal multiplication: n / d = umul64hi(n, ceil(2^64 / d)) for
 // n, d < 2^32 and d >= 2.
@@ -30,6 +31,7 @@ struct CellList {
     const uint32_t* idx;
     uint32_t count;
     unsigned long long rnx, rnxy;  // ceil(2^64 / nx), ceil(2^64 / (nx ny))
+    uint32_t n_begin, n_end;       // the processed cells (interior planes): n_begin <= n < n_end
 };
 
 // Per-run constants, derived on the host in FP64 from (tau, Theta, rho0, order) and rounded
@@ -92,7 +94,10 @@ struct Ops {
     cudaError_t (*step_pull)(const Geom&, const void* coef, const void* src, void* dst, int* flag, cudaStream_t);
     cudaError_t (*step_aa)(const Geom&, const void* coef, int odd, const void* src, void* dst, int* flag,
                            cudaStream_t);
-    // the AA step over a fluid-cell list (boxes with walls, FP16 storage)
+    // the pull step over a list of 16-cell sectors and the AA step over a fluid-cell list (boxes
+    // with walls, FP16 storage)
+    cudaError_t (*step_pull_sectors)(const Geom&, const void* coef, const CellList&, const void* src, void* dst,
+                                     int* flag, cudaStream_t);
     cudaError_t (*step_aa_list)(const Geom&, const void* coef, const CellList&, int odd, const void* src, void* dst,
                                 int* flag, cudaStream_t);
     cudaError_t (*moments)(const Geom&, const void* coef, int layout, const void* src, void* rho, void* u, void* Pi,

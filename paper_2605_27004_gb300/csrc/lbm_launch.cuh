@@ -125,6 +125,16 @@ struct Launch {
         return cudaGetLastError();
     }
 
+    static cudaError_t step_pull_sectors(const Geom& g, const void* coef, const CellList& L, const void* src,
+                                         void* dst, int* flag, cudaStream_t st) {
+        if (L.count == 0) return cudaSuccess;
+        const CF& cf = *static_cast<const CF*>(coef);
+        const unsigned long long threads = (unsigned long long)L.count * 16ull;
+        k_step_pull_sectors<Q, S><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g, cf, L, cpl(src, g), mpl(dst, g),
+                                                                                    flag);
+        return cudaGetLastError();
+    }
+
     static cudaError_t step_aa_list(const Geom& g, const void* coef, const CellList& L, int odd, const void* src,
                                     void* dst, int* flag, cudaStream_t st) {
         if (L.count == 0) return cudaSuccess;
@@ -294,8 +304,9 @@ struct Launch {
     }
 
     static const Ops& ops() {
-        static const Ops o = {&init,     &step_pull, &step_aa,   &step_aa_list, &moments, &totals, &adj_seed,
-                              &adj_step, &adj_init,  &link_mask, &ade_pull,     &ade_aa};
+        static const Ops o = {&init,     &step_pull, &step_aa,   &step_pull_sectors, &step_aa_list, &moments,
+                              &totals,   &adj_seed,  &adj_step,  &adj_init,          &link_mask,    &ade_pull,
+                              &ade_aa};
         return o;
     }
 };
