@@ -156,17 +156,20 @@ int lbm_record_checkpoints(lbm_ctx* ctx, int checkpoint_every);
  * lbm_init (else LBM_ERR_NO_FORWARD). Works backward in segments of checkpoint_every steps
  * (0: the recorded interval, else about sqrt(n)): each segment is recomputed from its checkpoint
  * (recorded by lbm_record_checkpoints, or taken here by a forward pass from the initial fields)
- * and then swept by one adjoint kernel per step. Host-memory checkpoints are copied back on a
- * second stream one segment ahead of use when one more state fits on the device. Leaves f(n) in
- * place. Results are read with lbm_gradients. The working set (two lambda arrays, the segment
- * states) is allocated by the first call and kept for later calls (an optimisation loop pays for
- * it once) until lbm_adjoint_release or lbm_destroy. Synchronises. */
+ * and then swept by one adjoint kernel per step; when the segment's states do not all fit on
+ * the device it is recomputed in sub-segments (the first pass keeps their starts and the last
+ * one's states, the others are recomputed again in their turn). Host-memory checkpoints are
+ * copied back on a second stream one segment ahead of use when one more state fits on the
+ * device. Leaves f(n) in place. Results are read with lbm_gradients. The working set (two lambda
+ * arrays, the segment states) is allocated by the first call and kept for later calls (an
+ * optimisation loop pays for it once) until lbm_adjoint_release or lbm_destroy. Synchronises. */
 int lbm_adjoint(lbm_ctx* ctx, const void* loss_grad, int n, int checkpoint_every);
 
-/* Plan of the last lbm_adjoint: sub_segment = the sub-segment length of a two-level
- * recompute (equal to checkpoint_every when segments are recomputed flat); prefetched = host
- * checkpoints copied back ahead of use. Either pointer may be NULL. No counterpart in the paper
- * (memory plan of the checkpointed adjoint). */
+/* Plan of the last lbm_adjoint: sub_segment = the longest sub-segment of a full segment when
+ * segments are recomputed in sub-segments (the states of fewer than checkpoint_every steps fit),
+ * else checkpoint_every (flat recompute); prefetched = host checkpoints copied back ahead of use.
+ * Either pointer may be NULL. No counterpart in the paper (memory plan of the checkpointed
+ * adjoint). */
 int lbm_adjoint_info(const lbm_ctx* ctx, int* sub_segment, int* prefetched);
 
 /* Free the adjoint's large working set (the lambda arrays and the segment states) that

@@ -534,6 +534,34 @@ int run_halo(lbm_ctx* c, int kind, void* array) {
     return LBM_OK;
 }
 
+// Recompute plan of one adjoint segment of `len` steps with W working state buffers. Flat
+// (len - 1 <= W): all states after the segment start are recomputed once and held. Otherwise the
+// segment is cut at starts 0 = s_0 < s_1 < ... < s_m < len: the first recompute pass keeps the
+// states s_1 .. s_(m-1) and every state of the last sub-segment [s_m, len) (L = len - s_m
+// buffers), which is swept first; each earlier sub-segment (at most L + 1 steps) is then
+// recomputed from its start into the last one's buffers and swept. W = (m - 1) + L buffers, and
+// the plan costs (len - 1) + (s_m - m) recompute steps, i.e. 2 len - 2 - W when m = W - L + 1:
+// every buffer saves one step, whatever L. The largest feasible L (fewest sub-segments) is
+// taken; L >= 2 so that the first pass can alternate two of the last sub-segment's buffers for
+// the states it does not keep. Returns false when W buffers admit no such plan; on success
+// `starts` holds s_0 .. s_m (just {0} when flat).
+bool segment_plan(int len, int W, std::vector<int>& starts) {
+    starts.assign(1, 0);
+    if (len - 1 <= W) return true;
+    for (int L = W; L >= 2; --L) {
+        const int rest = len - L;        // steps before the last sub-segment
+        const int m1 = W - L + 1;        // sub-segments the buffers allow before it
+        if ((long long)m1 * (L + 1) < rest) continue;
+        const int m = std::min(m1, rest);
+        for (int j = 0, s = 0; j < m; ++j) {
+            s += rest / m + (j < rest % m ? 1 : 0);
+            starts.push_back(s);
+        }
+        return true;
+    }
+    return false;
+}
+
 }  // namespace
 
 // =============================================================================================
@@ -946,31 +974,46 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
     const int C = (n + K - 1) / K;  // top-level checkpoints at t = 0, K, ..., (C-1)K
     const bool recorded = c->rec_K == K && c->rec_valid >= C;
 
-    // Memory plan for the states of one segment. Flat: the segment start plus its K-1 states.
-    // Two-level: sub-checkpoints every K2 steps of the segment plus the K2-1 states of one
-    // sub-segment, i.e. ceil(K/K2) + K2 - 1 buffers, at the price of a second recompute.
-    // Segment buffers are kept in the context for later calls, so they count as available.
+    // Memory plan for the states of one segment (segment_plan), next to bufs[0], the restore
+    // target of host checkpoints: flat when the K - 1 states fit; else, while the checkpoints are
+    // still to be taken, the fewest working buffers that admit a plan (device memory left to the
+    // checkpoints saves copies to and from the host), and over recorded checkpoints every buffer
+    // that fits, less one kept for restoring host checkpoints a segment ahead of use. Segment
+    // buffers are kept in the context for later calls, so they count as available.
     size_t fr = 0, tot = 0;
     LBM_CUDA(c, cudaMemGetInfo(&fr, &tot));
     const long long held = (long long)c->adj_bufs.size();
     size_t avail = (fr > ((size_t)1 << 30) ? fr - ((size_t)1 << 30) : 0) + (size_t)held * SB;
     if (c->opt.adjoint_mem_limit) avail = std::min(avail, c->opt.adjoint_mem_limit);
     const long long mbuf = (long long)(avail / SB);
-    auto need = [&](int k2) -> long long { return k2 >= K ? K : (K + k2 - 1) / k2 + k2 - 1; };
-    int K2 = K;
-    if (need(K) > mbuf) {
-        long long best = -1;
-        for (int k2 = 1; k2 < K; ++k2)
-            if (best < 0 || need(k2) < best) {
-                best = need(k2);
-                K2 = k2;
-            }
-        if (best > mbuf)
-            return fail(c, LBM_ERR_OOM, "adjoint: segment of %d steps needs %lld states of %zu bytes, %lld fit", K,
-                        best, SB, mbuf);
+    int W = K - 1;  // working state buffers besides bufs[0]
+    if (K > mbuf) {
+        int wmin = -1;
+        std::vector<int> sp;
+        for (int w = 2; w < K - 1 && wmin < 0; ++w)
+            if (segment_plan(K, w, sp)) wmin = w;
+        if (wmin < 0 || wmin + 1 > mbuf)
+            return fail(c, LBM_ERR_OOM, "adjoint: segment of %d steps needs %d states of %zu bytes, %lld fit", K,
+                        wmin < 0 ? K : wmin + 1, SB, mbuf);
+        W = wmin;
+        if (recorded) {
+            int n_dev = 0, n_host = 0;
+            for (int k = 0; k < C; ++k) (c->rec_host[k] ? n_host : n_dev) += 1;
+            long long budget = mbuf;  // the limit also covers the recorded device checkpoints
+            if (c->opt.adjoint_mem_limit)
+                budget = std::min<long long>(budget, (long long)(c->opt.adjoint_mem_limit / SB) - n_dev);
+            W = (int)std::max<long long>(wmin, std::min<long long>(K - 2, budget - 1 - (n_host > 1 ? 1 : 0)));
+        }
     }
-    const int S2 = (K + K2 - 1) / K2;
-    const int nbuf = (int)std::max<long long>(2, need(K2));
+    const bool flat_plan = W >= K - 1;
+    const int nbuf = std::max(2, W + 1);
+    int longest = K;  // longest sub-segment of a full segment, reported by lbm_adjoint_info
+    if (!flat_plan) {
+        std::vector<int> sp;
+        segment_plan(K, W, sp);
+        longest = K - sp.back();
+        for (size_t j = 0; j + 1 < sp.size(); ++j) longest = std::max(longest, sp[j + 1] - sp[j]);
+    }
 
     std::vector<void*> ckpt(C, nullptr);
     std::vector<bool> ckpt_host(C, false);
@@ -1145,7 +1188,7 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
     // not a restore target), and no halo callbacks between the kernels.
     int n_host_ckpt = 0;
     for (int k = 0; k < C; ++k) n_host_ckpt += ckpt_host[k] ? 1 : 0;
-    const bool seg_graphs = K2 >= K && K % 2 == 0 && K >= 2 && n_host_ckpt == 0 && !c->slab &&
+    const bool seg_graphs = flat_plan && K % 2 == 0 && K >= 2 && n_host_ckpt == 0 && !c->slab &&
                             (c->opt.use_graphs > 0 || (c->opt.use_graphs == 0 && c->N <= (1LL << 21)));
     auto capture_segment = [&](long long t0) -> int {
         if (!c->cap_stream) LBM_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
@@ -1196,38 +1239,45 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
             if (!seg_graph) LBM_ADJ_RC(capture_segment(t0));
             LBM_ADJ_CHECK(cudaGraphLaunch(seg_graph, c->stream), "segment graph launch");
             c->launches += 2 * K - 1;  // K even: lc is back at its value at the segment start
-        } else if (K2 >= K) {  // flat: states t0 + j in bufs[j], j = 1 .. len-1
-            std::vector<const void*> st(len);
-            st[0] = start;
-            for (int j = 1; j < len; ++j) {
-                LBM_ADJ_RC(step_oop(st[j - 1], bufs[j], t0 + j - 1, "segment recompute"));
-                st[j] = bufs[j];
-            }
-            LBM_ADJ_RC(sweep(st, t0));
-        } else {  // two-level: sub-checkpoints in bufs[1 .. S2-1], sub-segment states after them
-            std::vector<const void*> sub(S2);
-            sub[0] = start;
-            void** subseg = bufs + S2;
-            const int nsub = (len + K2 - 1) / K2;
-            for (int j = 1; j < nsub; ++j) {
-                const void* cur = sub[j - 1];
-                for (int i = 1; i <= K2; ++i) {
-                    void* dst = i == K2 ? bufs[j] : subseg[i - 1];
-                    LBM_ADJ_RC(step_oop(cur, dst, t0 + (long long)(j - 1) * K2 + i - 1, "sub-checkpoint recompute"));
+        } else {
+            std::vector<int> sp;
+            segment_plan(len, W, sp);  // W admits a plan for K >= len steps
+            const int m = (int)sp.size() - 1;
+            if (m == 0) {  // flat: states t0 + j in bufs[j], j = 1 .. len-1
+                std::vector<const void*> st(len);
+                st[0] = start;
+                for (int j = 1; j < len; ++j) {
+                    LBM_ADJ_RC(step_oop(st[j - 1], bufs[j], t0 + j - 1, "segment recompute"));
+                    st[j] = bufs[j];
+                }
+                LBM_ADJ_RC(sweep(st, t0));
+            } else {  // states s_1 .. s_(m-1) in bufs[1 .. m-1], the last sub-segment in bufs[m ..]
+                void** last = bufs + m;
+                const int L = len - sp[m];
+                const void* cur = start;
+                for (int i = 1, j = 1; i < len; ++i) {
+                    void* dst;
+                    if (j < m && i == sp[j])
+                        dst = bufs[j++];
+                    else if (i >= sp[m])
+                        dst = last[i - sp[m]];
+                    else  // not kept: alternate the last two buffers, state s_m - 1 in last[L - 1]
+                        dst = last[L - 1 - ((sp[m] - 1 - i) & 1)];
+                    LBM_ADJ_RC(step_oop(cur, dst, t0 + i - 1, "sub-checkpoint recompute"));
                     cur = dst;
                 }
-                sub[j] = bufs[j];
-            }
-            for (int j = nsub - 1; j >= 0; --j) {
-                const long long t1 = t0 + (long long)j * K2;
-                const int len2 = (int)std::min<long long>(K2, t0 + len - t1);
-                std::vector<const void*> st(len2);
-                st[0] = sub[j];
-                for (int i = 1; i < len2; ++i) {
-                    LBM_ADJ_RC(step_oop(st[i - 1], subseg[i - 1], t1 + i - 1, "segment recompute"));
-                    st[i] = subseg[i - 1];
+                std::vector<const void*> st(last, last + L);
+                LBM_ADJ_RC(sweep(st, t0 + sp[m]));
+                for (int j = m - 1; j >= 0; --j) {
+                    const int lj = sp[j + 1] - sp[j];  // <= L + 1
+                    st.assign(lj, nullptr);
+                    st[0] = j == 0 ? start : bufs[j];
+                    for (int i = 1; i < lj; ++i) {
+                        LBM_ADJ_RC(step_oop(st[i - 1], last[i - 1], t0 + sp[j] + i - 1, "segment recompute"));
+                        st[i] = last[i - 1];
+                    }
+                    LBM_ADJ_RC(sweep(st, t0 + sp[j]));
                 }
-                LBM_ADJ_RC(sweep(st, t1));
             }
         }
     }
@@ -1251,7 +1301,7 @@ int lbm_adjoint(lbm_ctx* c, const void* loss_grad, int n, int K) {
     }
     c->grad_tau = c->hout[6];
     c->grads_ready = true;
-    c->last_adj_K2 = K2;
+    c->last_adj_K2 = longest;
     c->last_adj_prefetch = prefetched;
     release();
     return LBM_OK;

@@ -137,11 +137,14 @@ def test_recorded_and_host_checkpoints_give_identical_gradients(scheme):
         assert np.array_equal(dth, out[0][0]) and dtau == out[0][1] and torch.equal(du0, out[0][2])
 
 
-@pytest.mark.parametrize("scheme,recorded", [("pull", False), ("aa", True)])
-def test_two_level_segments_match_flat(scheme, recorded):
-    """When K segment states do not fit (adjoint_mem_limit), segments are recomputed in two
-    levels (sub-checkpoints every K2 steps); the states and the kernel order are the same, so the
-    gradients are bit-identical to the flat plan."""
+@pytest.mark.parametrize("scheme,recorded,limits", [("pull", False, (0, 6, 9)), ("aa", True, (0, 6, 8, 9, 11))])
+def test_two_level_segments_match_flat(scheme, recorded, limits):
+    """When K segment states do not fit (adjoint_mem_limit), a segment is recomputed in
+    sub-segments: the first pass keeps the sub-segment starts and the states of the last one,
+    the others are recomputed into its buffers. The states and the kernel order are the same
+    as in the flat plan, so the gradients are bit-identical. Over recorded checkpoints every
+    state buffer that fits is used (limits of 6, 8, 9 and 11 states give 5, 6, 7 and 8 working
+    buffers: sub-segments (4, 4, 4), (6, 6), (5, 7) and (4, 8) of K = 12)."""
     import torch
     from paper_2605_27004_gb300 import lbm
     q, dims, steps, K = 27, (18, 12, 10), 29, 12
@@ -153,17 +156,24 @@ def test_two_level_segments_match_flat(scheme, recorded):
     g = torch.as_tensor(np.random.default_rng(98).standard_normal((3, N)) * (1 - solid)[None, :], dtype=torch.float32)
     SB = q * N * 4
     out = []
-    for limit in (0, 6 * SB):
-        L = lbm.LBM(q, *dims, 0.7, Th, solid=solid, storage="fp32", scheme=scheme, adjoint_mem_limit=limit)
+    longest = []
+    for limit in limits:
+        L = lbm.LBM(q, *dims, 0.7, Th, solid=solid, storage="fp32", scheme=scheme, adjoint_mem_limit=limit * SB)
         if recorded:
             L.record_checkpoints(K)
         L.init(torch.as_tensor(rho0), torch.as_tensor(u0))
         L.step(steps)
-        L.adjoint(g, steps, K)
-        assert (L.adjoint_info()[0] < K) == (limit > 0)
-        dth, dtau, du0 = L.gradients()
-        out.append((dth, dtau, du0.cpu()))
-    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1] and torch.equal(out[0][2], out[1][2])
+        for _ in range(2):  # the second call reuses the kept buffers
+            L.adjoint(g, steps, K)
+            dth, dtau, du0 = L.gradients()
+            out.append((dth, dtau, du0.cpu()))
+        longest.append(L.adjoint_info()[0])
+        L.close()
+    for dth, dtau, du0 in out[1:]:
+        assert np.array_equal(out[0][0], dth) and out[0][1] == dtau and torch.equal(out[0][2], du0)
+    assert longest[0] == K and all(k < K for k in longest[1:])
+    if recorded:
+        assert longest == [12, 4, 6, 7, 8]
     with pytest.raises(lbm.LBMError) as e:   # even the two-level plan needs 6 states for K = 12
         L = lbm.LBM(q, *dims, 0.7, Th, solid=solid, storage="fp32", scheme=scheme, adjoint_mem_limit=5 * SB)
         L.init(torch.as_tensor(rho0), torch.as_tensor(u0))
