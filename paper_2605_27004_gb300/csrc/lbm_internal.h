@@ -70,12 +70,12 @@ Shape shape_for(const Geom& g, int nzp);
 // threads stay full: a kernel limited to two blocks per SM by its registers keeps 16 warps),
 // then the widest. 384 threads per row run as three 128 x 2 blocks instead of two 256-thread
 // blocks a quarter of which idle; 192 as 64 x 4 rather than 192 x 1.
-inline int block_x_for(int n) {
+inline int block_x_for(int n, int threads = 256) {
     int best = 32, waste = 1 << 30;
     bool full = true;
-    for (int bx = 256; bx >= 32; bx -= 32) {
+    for (int bx = threads; bx >= 32; bx -= 32) {
         const int w = ((n + bx - 1) / bx) * bx - n;
-        const bool f = 256 % bx == 0;
+        const bool f = threads % bx == 0;
         if (w < waste || (w == waste && f && !full)) {
             waste = w;
             best = bx;

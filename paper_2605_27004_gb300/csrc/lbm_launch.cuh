@@ -44,7 +44,8 @@ struct Launch {
     }
 
     // Two cells per thread pay off where the one-cell kernel is instruction-bound: FP16 storage
-    // without walls (measured at 256^3: D3Q19 0.61 -> 0.82, D3Q27 0.70 -> 0.75 of the copy peak).
+    // without walls (measured at 256^3: D3Q19 0.61 -> 0.82, D3Q27 0.70 -> 0.83 of the copy peak,
+    // the D3Q27 kernels in 128-thread blocks, see pair_threads).
     // FP32 storage is at the bandwidth bound with one cell per thread already, and the wall
     // variants lose occupancy.
     static bool pairs(const Geom& g) { return S == 3 && !g.link && (g.nx % 2) == 0; }
@@ -70,7 +71,7 @@ struct Launch {
                 }
             }
             if (pairs(g)) {
-                const Shape sp = shape_pairs(g);
+                const Shape sp = shape_pairs(g, pair_threads<Q>());
                 k_step_pull2<Q, S, false><<<sp.grid, sp.block, 0, st>>>(g, cf, VelField<float>{}, a, b, flag);
                 return cudaGetLastError();
             }
@@ -89,9 +90,7 @@ struct Launch {
         const auto a = cpl(src, g);
         const auto b = mpl(dst, g);
         if constexpr (S == 3) {  // pairs(g) holds for FP16 r-shifted storage only
-            // no walls (see pairs()); the D3Q27 odd step runs one cell per thread: its pair kernel
-            // scatters 18 x-shifted planes as single elements at 126 registers (two blocks per
-            // SM), measured 0.68 -> 0.70 (256^3) and 0.69 -> 0.71 (384^3) of the copy peak
+            // no walls (see pairs())
             if constexpr (Q != 27) {
                 if (quads(g)) {
                     const Shape sq = shape_quads(g);
@@ -102,8 +101,8 @@ struct Launch {
                     return cudaGetLastError();
                 }
             }
-            if (pairs(g) && !(Q == 27 && odd)) {
-                const Shape sp = shape_pairs(g);
+            if (pairs(g)) {
+                const Shape sp = shape_pairs(g, pair_threads<Q>());
                 if (odd)
                     k_step_aa_odd2<Q, S><<<sp.grid, sp.block, 0, st>>>(g, cf, VelField<float>{}, a, b, flag);
                 else
@@ -249,7 +248,7 @@ struct Launch {
                 }
             }
             if (pairs(g)) {
-                const Shape sp = shape_pairs(g);
+                const Shape sp = shape_pairs(g, pair_threads<Q>());
                 k_step_pull2<Q, S, false, true><<<sp.grid, sp.block, 0, st>>>(g, cf, vel_field(u, g), cpl(src, g),
                                                                             mpl(dst, g), flag);
                 return cudaGetLastError();
@@ -281,7 +280,7 @@ struct Launch {
                 }
             }
             if (pairs(g)) {
-                const Shape sp = shape_pairs(g);
+                const Shape sp = shape_pairs(g, pair_threads<Q>());
                 if (odd)
                     k_step_aa_odd2<Q, S, true><<<sp.grid, sp.block, 0, st>>>(g, cf, v, a, b, flag);
                 else

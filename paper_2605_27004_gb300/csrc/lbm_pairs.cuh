@@ -253,10 +253,19 @@ __device__ __forceinline__ bool collide2(const Coef<float>& cf, const VelField<f
 }
 
 // ---------------------------------------------------------------------------------------------
-// Pull step, two cells per thread.
+// Pull step, two cells per thread. The D3Q27 pair kernels run blocks of 128 threads, five per SM
+// at 96 registers (8-48 bytes of spills): 20 resident warps instead of 16 with two 256-thread
+// blocks at 126 registers, measured at 256^3 / 384^3 pull 0.774 -> 0.828 / 0.780 -> 0.827 of the
+// copy peak, AA 0.715 -> 0.788 / 0.728 -> 0.787 (which also moved the odd AA step from one cell
+// per thread to pairs).
 // ---------------------------------------------------------------------------------------------
+template <int Q>
+constexpr int pair_threads() {
+    return Q == 27 ? 128 : 256;
+}
+
 template <int Q, int S, bool MASK, bool ADE = false>
-__global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3)
+__global__ void __launch_bounds__(pair_threads<Q>(), Q == 27 ? 5 : (S != 3 ? 2 : 3))
     k_step_pull2(Geom g, Coef<float> cf, VelField<float> vf, const Planes<const typename Store<S>::type> src,
                  const Planes<typename Store<S>::type> dst, int* __restrict__ flag) {
     PCell c;
@@ -297,7 +306,7 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3)
 // AA even step (state LOCAL -> AAODD), two cells per thread: purely local.
 // ---------------------------------------------------------------------------------------------
 template <int Q, int S, bool MASK, bool ADE = false>
-__global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3)
+__global__ void __launch_bounds__(pair_threads<Q>(), Q == 27 ? 5 : (S != 3 ? 2 : 3))
     k_step_aa_even2(Geom g, Coef<float> cf, VelField<float> vf, const Planes<const typename Store<S>::type> src,
                     const Planes<typename Store<S>::type> dst, int* __restrict__ flag) {
     PCell c;
@@ -336,7 +345,7 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3)
 // element is never used by the fetching thread.)
 // ---------------------------------------------------------------------------------------------
 template <int Q, int S, bool ADE = false>
-__global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3)
+__global__ void __launch_bounds__(pair_threads<Q>(), Q == 27 ? 5 : (S != 3 ? 2 : 3))
     k_step_aa_odd2(Geom g, Coef<float> cf, VelField<float> vf, const Planes<const typename Store<S>::type> src,
                    const Planes<typename Store<S>::type> dst, int* __restrict__ flag) {
     PCell c;
@@ -371,11 +380,11 @@ __global__ void __launch_bounds__(256, (Q == 27 || S != 3) ? 2 : 3)
     }
 }
 
-inline Shape shape_pairs(const Geom& g) {
+inline Shape shape_pairs(const Geom& g, int threads = 256) {
     Shape s;
     const int np = g.nx / 2;
-    const int bx = block_x_for(np);
-    const int by = std::max(1, 256 / bx);
+    const int bx = block_x_for(np, threads);
+    const int by = std::max(1, threads / bx);
     s.block = dim3(bx, by, 1);
     s.grid = dim3((np + bx - 1) / bx, (g.ny + by - 1) / by, g.nz - 2 * LBM_SLAB);
     s.nblocks = (long long)s.grid.x * s.grid.y * s.grid.z;
