@@ -485,8 +485,10 @@ __global__ void __launch_bounds__(256) k_step_aa(Geom g, Coef<typename Store<S>:
 // FP16 storage with walls, where the one-cell kernels are limited by issued instructions and the
 // solid lanes of mixed warps (about 30 % of the lanes in the porous medium) issue them too
 // (porous D3Q27 512^3: 0.465 -> 0.483 of the copy peak on fluid accounting). The in-place AA
-// kernels store fluid slots only anyway; for the pull scheme the list loses the whole-sector
-// stores of the grid kernel (measured 0.443 -> 0.384) and is not used.
+// kernels store fluid slots only anyway; for the pull scheme a fluid-cell list loses the
+// whole-sector stores of the grid kernel (measured 0.443 -> 0.384), so the pull step runs over
+// 16-cell sectors instead (k_step_pull_sectors). Four blocks per SM (64 registers; the odd step
+// had taken 77, three blocks): 0.483 -> 0.490.
 // ---------------------------------------------------------------------------------------------
 // Cell n of the list's box, its coordinates from the exact reciprocals of nx and nx ny.
 __device__ __forceinline__ void make_cell_index(const Geom& g, const CellList& L, uint32_t n, Cell& c) {
@@ -559,7 +561,7 @@ __global__ void __launch_bounds__(256) k_step_pull_sectors(Geom g, Coef<typename
 }
 
 template <int Q, int S, int ODD>
-__global__ void __launch_bounds__(256) k_step_aa_list(Geom g, Coef<typename Store<S>::T> cf, CellList L,
+__global__ void __launch_bounds__(256, 4) k_step_aa_list(Geom g, Coef<typename Store<S>::T> cf, CellList L,
                                                       const Planes<const typename Store<S>::type> src,
                                                       const Planes<typename Store<S>::type> dst,
                                                       int* __restrict__ flag) {

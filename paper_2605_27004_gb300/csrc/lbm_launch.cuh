@@ -193,7 +193,7 @@ struct Launch {
         const CF& cf = *static_cast<const CF*>(coef);
         if constexpr (S == 3 && Q != 27) {  // FP16 storage without walls: two cells per thread (lbm_adjoint2.cuh;
             // D3Q27 stays one cell per thread: at 128 registers the pair kernel would spill)
-            const Shape sp = shape_pairs(g);
+            const Shape sp = shape_pairs(g, 128);  // the block shape k_adj_step2 is built for
             if (!g.link && (g.nx % 2) == 0 && sp.nblocks <= sh.nblocks) {  // records fit the per-cell grid's
                 const auto a = cpl(src, g);
                 const auto ln = cfl(lam_next, g);
