@@ -200,7 +200,7 @@ def test_error_paths():
 # fallback), ragged ny and nz = 1
 PAIR_GEOMS = [(19, (2, 5, 4)), (19, (64, 3, 3)), (19, (130, 3, 2)), (19, (46, 13, 9)), (27, (38, 11, 10)),
               (9, (98, 21, 1)), (19, (45, 7, 6)), (19, (128, 7, 5)), (27, (256, 5, 3)), (9, (384, 9, 1)),
-              (19, (256, 3, 4))]
+              (19, (256, 3, 4)), (27, (100, 6, 5))]
 
 
 @pytest.mark.parametrize("q,dims", PAIR_GEOMS)
