@@ -14,6 +14,7 @@ Modes
   --mode sweep     one JSON line per variant (lattice x storage x scheme x size, porous runs).
   --mode profile   a small case of one kernel for ncu (--lattice/--storage/--scheme/--n/--kernel).
   --mode slabs     the z-slab decomposition on one GPU against the whole box (--n, --storage).
+  --mode oracle    the FP64 oracle on a bounded sample of each workload (host cores, no GPU).
   --sharded        the contract line for one box cut into z-slabs over the ranks (strong scaling,
                    halo exchange over torch.distributed) instead of independent replicas.
   --impl reference the oracle itself timed on the host cores (the reference arm).
@@ -340,6 +341,53 @@ def cpu_baseline(budget_s=12.0):
             "sample": f"D3Q19 Taylor-Green on a 64^3 box, {steps} steps of the FP64 push oracle"}
 
 
+def _timed_oracle_steps(pb, f, budget_s):
+    """As many steps of the oracle on f as fit the budget (one step timed first); (steps, s)."""
+    t = time.perf_counter()
+    pb.run(f, 1)
+    one = time.perf_counter() - t
+    steps = max(1, int(budget_s / max(one, 1e-4)))
+    t = time.perf_counter()
+    pb.run(f, steps)
+    return steps, time.perf_counter() - t
+
+
+def oracle_per_config(budget_s=8.0):
+    """The FP64 oracle as it stands, on a bounded sample of each workload: rows of
+    (config, MLUPS, sample). Forward samples count every cell updated; the adjoint sample counts
+    adjoint time steps (the oracle keeps all states and runs its own forward pass)."""
+    import oracle
+    from paper_2605_27004_gb300 import inputs
+    rows = []
+    rho0, u0 = inputs.shear_wave_2d(64, 64, 0.01, 1e-4)
+    pb = oracle.Problem(9, 64, 64, 1, 0.8, np.array([[0.36, 0.02], [0.02, 0.30]]))
+    steps, dt = _timed_oracle_steps(pb, pb.init(rho0, u0), budget_s)
+    rows.append(("1 D2Q9 FP64 64^2 shear wave", 64 * 64 * steps / dt / 1e6, f"the full 64^2 box, {steps} steps"))
+    dims, tau, Th, rho0, u0, _ = problem(19, 64, "tg")
+    pb = oracle.Problem(19, *dims, tau, Th)
+    steps, dt = _timed_oracle_steps(pb, pb.init(rho0, u0), budget_s)
+    rows.append(("2 D3Q19 Taylor-Green", 64 ** 3 * steps / dt / 1e6, f"a 64^3 box, {steps} steps"))
+    dims, tau, Th, rho0, u0, solid = problem(27, 64, "porous")
+    pb = oracle.Problem(27, *dims, tau, Th, solid=solid)
+    steps, dt = _timed_oracle_steps(pb, pb.init(rho0, u0), budget_s)
+    nf = int((np.asarray(solid) == 0).sum())
+    rows.append(("3 D3Q27 porous, walls", nf * steps / dt / 1e6,
+                 f"a 64^3 porous box of the same recipe ({nf} fluid cells), {steps} steps, fluid-cell MLUPS"))
+    _, u0 = inputs.random_fourier_modes(32, 4.0, 0.02)
+    pb = oracle.Problem(19, 32, 32, 32, 0.6, np.eye(3) / 3)
+    g = np.random.default_rng(inputs.SEED_BASE + 4).standard_normal((3, 32 ** 3))
+    t = time.perf_counter()
+    pb.adjoint(np.ones(32 ** 3), u0, 2, g)
+    one = (time.perf_counter() - t) / 2
+    steps = max(2, int(budget_s / max(one, 1e-4)))
+    t = time.perf_counter()
+    pb.adjoint(np.ones(32 ** 3), u0, steps, g)
+    dt = time.perf_counter() - t
+    rows.append(("4 D3Q19 adjoint (forward pass, all states kept, reverse sweep)", 32 ** 3 * steps / dt / 1e6,
+                 f"a 32^3 box, {steps} adjoint steps"))
+    return rows
+
+
 def job_throughput(ms_local, cells, steps, dist, torch, device="cuda"):
     """Whole-job throughput of independent replicas (one per rank): the slowest rank's time (MAX
     over ranks) and the cells all ranks updated, cells x steps x world size, per second in MLUPS.
@@ -562,7 +610,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="bench", choices=["bench", "sweep", "profile", "slabs"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "sweep", "profile", "slabs", "oracle"])
     ap.add_argument("--no-extras", action="store_true", help="contract line without sub-measurements/e2e/cpu")
     ap.add_argument("--only", default="", help="sweep: substring filter on case names")
     ap.add_argument("--lattice", type=int, default=19)
@@ -578,6 +626,12 @@ def main():
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.mode == "oracle":  # the oracle on a bounded sample of each workload (host cores only)
+        import oracle
+        for cfg, v, sample in oracle_per_config():
+            print(json.dumps({"oracle": True, "config": cfg, "value": v, "unit": "MLUPS", "cores": oracle.threads(),
+                              "kind": "oracle", "sample": sample}), flush=True)
         return
 
     import torch

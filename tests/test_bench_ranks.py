@@ -60,3 +60,13 @@ def test_reference_arm_other_ranks_exit_without_output():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "1"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_oracle_per_config_rows():
+    """The per-workload oracle timing (bench.py --mode oracle): one positive MLUPS row for each
+    of the four workloads, on a tiny budget."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rows = bench.oracle_per_config(budget_s=0.05)
+    assert [r[0][0] for r in rows] == ["1", "2", "3", "4"]
+    assert all(r[1] > 0 for r in rows)
