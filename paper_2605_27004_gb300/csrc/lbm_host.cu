@@ -134,7 +134,7 @@ struct lbm_ctx {
     Shape shape{};
     uint32_t* link = nullptr;  // per-cell link words (N), null for an all-fluid box
     long long n_fluid = 0;
-    uint32_t* cell_idx = nullptr;  // FP16 with walls: fluid cells (AA) or 16-cell sectors (pull)
+    uint32_t* cell_idx = nullptr;  // with walls: fluid cells (FP16 AA) or 32-byte sectors (FP16 / FP32 pull)
     CellList cells{};
 
     Coef<double> cd{};
@@ -336,7 +336,7 @@ void drop_graph(lbm_ctx* c) {
 }
 
 // One forward step src -> dst of a flow context on stream s (t = steps done before it): over the
-// lists of an FP16 context with walls (sectors for pull, cells for AA), else over the grid.
+// lists of a context with walls (sectors for pull, cells for FP16 AA), else over the grid.
 cudaError_t step_kernel(lbm_ctx* c, const void* src, void* dst, long long t, cudaStream_t s) {
     if (c->cell_idx)
         return c->scheme == LBM_PULL2
@@ -741,10 +741,15 @@ int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau
             dev_free(c, dmask, (size_t)c->N);
             if (e != cudaSuccess) return bail(cuda_fail(c, e, "link-mask construction"));
             c->geom.link = c->link;
-            // FP16 storage is limited by issued instructions: list the fluid cells (AA: no lane of a
-            // warp belongs to a solid cell) or the 16-cell sectors that hold one (pull: the stores
-            // stay whole sectors), over the interior planes only
-            if ((c->storage == LBM_FP16_SHIFTED || c->storage == LBM_FP16_WSHIFTED) && nx >= 2) {
+            // Lists over the interior planes. FP16 storage is limited by issued instructions: the AA
+            // steps run over the fluid cells (no lane of a warp belongs to a solid cell), the pull
+            // step over the 32-byte sectors (16 cells) that hold a fluid cell (its stores stay whole
+            // sectors). The FP32 pull step runs over its 8-cell sectors the same way, so that no
+            // warp slot is spent on a sector of solid cells only (porous D3Q27 512^3: 0.714 ->
+            // 0.750 of the copy peak on fluid accounting).
+            const bool fp16 = c->storage == LBM_FP16_SHIFTED || c->storage == LBM_FP16_WSHIFTED;
+            const bool fp32 = c->storage == LBM_FP32 || c->storage == LBM_FP32_SHIFTED;
+            if ((fp16 || (fp32 && c->scheme == LBM_PULL2)) && nx >= 2) {
                 std::vector<uint32_t> idx;
                 const long long z0 = c->slab ? 1 : 0;
                 const long long nb = z0 * plane, ne = (z0 + nz) * plane;
@@ -753,9 +758,10 @@ int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau
                     for (long long n = nb; n < ne; ++n)
                         if (!m[(size_t)n]) idx.push_back((uint32_t)n);
                 } else {
-                    for (long long s0 = nb / 16; s0 * 16 < ne; ++s0) {
+                    const long long G = fp16 ? 16 : 8;  // cells of one 32-byte sector
+                    for (long long s0 = nb / G; s0 * G < ne; ++s0) {
                         bool any = false;
-                        for (long long n = std::max(s0 * 16, nb); n < std::min(s0 * 16 + 16, ne) && !any; ++n)
+                        for (long long n = std::max(s0 * G, nb); n < std::min(s0 * G + G, ne) && !any; ++n)
                             any = !m[(size_t)n];
                         if (any) idx.push_back((uint32_t)s0);
                     }

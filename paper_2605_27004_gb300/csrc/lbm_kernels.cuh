@@ -521,20 +521,23 @@ __device__ __forceinline__ bool make_cell_list(const Geom& g, const CellList& L,
     return true;
 }
 
-// Pull step over the list of 16-cell sectors that hold a fluid cell: each half-warp takes one
-// sector, so a warp never spends lanes on sectors of solid cells only (11 % of the FP16 sectors
-// of the porous medium, against 2 % of whole solid warps in the grid kernel), and its stores stay
-// whole sectors as in k_step_pull (solid lanes store zeros into their never-read slots). Lanes
-// past the processed planes (the ends of the list) load and store nothing.
+// Pull step over the list of 32-byte sectors (16 FP16 or 8 FP32 cells of a plane) that hold a
+// fluid cell: G consecutive lanes take one sector, so a warp never spends lanes on sectors of solid
+// cells only (11 % of the FP16 sectors of the porous medium, against 2 % of whole solid warps in
+// the grid kernel), and its stores stay whole sectors as in k_step_pull (solid lanes store zeros
+// into their never-read slots). Lanes past the processed planes (the ends of the list) load and
+// store nothing. Ordering the list so that sectors without wall links come first in each window
+// of 32 (more warps on the branch-free gather) measured +0.25 % and is not done.
 template <int Q, int S>
 __global__ void __launch_bounds__(256) k_step_pull_sectors(Geom g, Coef<typename Store<S>::T> cf, CellList L,
                                                            const Planes<const typename Store<S>::type> src,
                                                            const Planes<typename Store<S>::type> dst,
                                                            int* __restrict__ flag) {
     using T = typename Store<S>::T;
+    constexpr uint32_t G = 32u / sizeof(typename Store<S>::type);
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t sec = t >> 4;
-    uint32_t n = sec < L.count ? __ldg(L.idx + sec) * 16u + (t & 15u) : 0u;
+    const uint32_t sec = t / G;
+    uint32_t n = sec < L.count ? __ldg(L.idx + sec) * G + (t % G) : 0u;
     const bool valid = sec < L.count && n >= L.n_begin && n < L.n_end;
     if (!valid) n = L.n_begin;
     Cell c;

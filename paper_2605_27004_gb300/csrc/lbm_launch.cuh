@@ -128,7 +128,7 @@ struct Launch {
                                          void* dst, int* flag, cudaStream_t st) {
         if (L.count == 0) return cudaSuccess;
         const CF& cf = *static_cast<const CF*>(coef);
-        const unsigned long long threads = (unsigned long long)L.count * 16ull;
+        const unsigned long long threads = (unsigned long long)L.count * (32ull / sizeof(ST));  // a sector each
         k_step_pull_sectors<Q, S><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g, cf, L, cpl(src, g), mpl(dst, g),
                                                                                     flag);
         return cudaGetLastError();
