@@ -73,6 +73,43 @@ __global__ void __launch_bounds__(256)
     for (int i = 0; i < Q; ++i) st_raw(dst.p[i] + c.n, solid ? T(0) : from_shifted<S>(d[i], cf.so[i]));
 }
 
+// The scalar pull step with walls over the list of 32-byte sectors that hold a fluid cell (as
+// k_step_pull_sectors for the flow; FP16 and FP32 storage).
+template <int Q, int S>
+__global__ void __launch_bounds__(256)
+    k_ade_pull_sectors(Geom g, Coef<typename Store<S>::T> cf, CellList L, VelField<typename Store<S>::T> vf,
+                       const Planes<const typename Store<S>::type> src, const Planes<typename Store<S>::type> dst,
+                       int* __restrict__ flag) {
+    using T = typename Store<S>::T;
+    constexpr uint32_t G = 32u / sizeof(typename Store<S>::type);
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t sec = t / G;
+    uint32_t n = sec < L.count ? __ldg(L.idx + sec) * G + (t % G) : 0u;
+    const bool valid = sec < L.count && n >= L.n_begin && n < L.n_end;
+    if (!valid) n = L.n_begin;
+    Cell c;
+    make_cell_index(g, L, n, c);
+    const uint32_t lw = valid ? __ldg(g.link + c.n) : LINK_SOLID;
+    const bool solid = (lw & LINK_SOLID) != 0u;
+    const unsigned act = __activemask();
+    if (__all_sync(act, solid)) return;
+    T d[Q];
+    if (__all_sync(act, lw == 0u)) {
+        gather<Q, S, false, LAYOUT_PULL, true>(c, 0u, cf, src, d);
+    } else if (!solid) {
+        gather<Q, S, true, LAYOUT_PULL, true>(c, lw, cf, src, d);
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = T(0);
+    }
+    const T s = ade_bgk<Q, T>(cf, vf, c.n, d);
+    if (!solid && !isfinite(s)) *flag = 1;
+    const bool store = store_group<typename Store<S>::type>(act, solid);
+    if (!valid || !store) return;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st_raw(dst.p[i] + c.n, solid ? T(0) : from_shifted<S>(d[i], cf.so[i]));
+}
+
 // AA pattern in place (see k_step_aa): even steps read and write the own cell, odd steps the
 // neighbours along +c_i.
 template <int Q, int S, bool MASK, int ODD>

@@ -359,7 +359,9 @@ cudaError_t launch_step(lbm_ctx* c, cudaStream_t s) {
     if (c->kind == 1) {
         const void* u = c->ade_u_zero ? nullptr : c->ade_u;
         if (c->scheme == LBM_PULL2) {
-            e = c->ops->ade_pull(c->geom, c->coef(), u, c->pop[c->cur], c->pop[c->cur ^ 1], c->flag, s);
+            e = c->cell_idx ? c->ops->ade_pull_sectors(c->geom, c->coef(), c->cells, u, c->pop[c->cur],
+                                                       c->pop[c->cur ^ 1], c->flag, s)
+                            : c->ops->ade_pull(c->geom, c->coef(), u, c->pop[c->cur], c->pop[c->cur ^ 1], c->flag, s);
             c->cur ^= 1;
         } else {
             e = c->ops->ade_aa(c->geom, c->coef(), u, (int)(c->steps & 1), c->pop[0], c->pop[0], c->flag, s);
@@ -744,12 +746,14 @@ int lbm_create_ex(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau
             // Lists over the interior planes. FP16 storage is limited by issued instructions: the AA
             // steps run over the fluid cells (no lane of a warp belongs to a solid cell), the pull
             // step over the 32-byte sectors (16 cells) that hold a fluid cell (its stores stay whole
-            // sectors). The FP32 pull step runs over its 8-cell sectors the same way, so that no
-            // warp slot is spent on a sector of solid cells only (porous D3Q27 512^3: 0.714 ->
-            // 0.750 of the copy peak on fluid accounting).
+            // sectors). The D3Q27 FP32 pull step runs over its 8-cell sectors the same way, so that
+            // no warp slot is spent on a sector of solid cells only (porous D3Q27 512^3: 0.714 ->
+            // 0.750 of the copy peak on fluid accounting; the scalar at 256^3 0.706 -> 0.738); the
+            // lighter D3Q19 FP32 cell update lost by it (scalar, 512^3: 0.708 -> 0.668) and stays on
+            // the grid.
             const bool fp16 = c->storage == LBM_FP16_SHIFTED || c->storage == LBM_FP16_WSHIFTED;
             const bool fp32 = c->storage == LBM_FP32 || c->storage == LBM_FP32_SHIFTED;
-            if ((fp16 || (fp32 && c->scheme == LBM_PULL2)) && nx >= 2) {
+            if ((fp16 || (fp32 && c->q == 27 && c->scheme == LBM_PULL2)) && nx >= 2) {
                 std::vector<uint32_t> idx;
                 const long long z0 = c->slab ? 1 : 0;
                 const long long nb = z0 * plane, ne = (z0 + nz) * plane;
@@ -1472,10 +1476,11 @@ int lbm_ade_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, double ta
     if (rc == LBM_OK) {
         lbm_ctx* c = *out;
         c->kind = 1;
-        // the scalar's step kernels run over the grid: no fluid-cell list
-        dev_free(c, c->cell_idx, (size_t)c->cells.count * 4 + 4);
-        c->cell_idx = nullptr;
-        c->cells = CellList{};
+        if (c->scheme != LBM_PULL2) {  // the scalar's AA steps run over the grid: no fluid-cell list
+            dev_free(c, c->cell_idx, (size_t)c->cells.count * 4 + 4);
+            c->cell_idx = nullptr;
+            c->cells = CellList{};
+        }
     }
     return rc;
 }

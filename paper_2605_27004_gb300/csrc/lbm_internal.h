@@ -94,8 +94,8 @@ struct Ops {
     cudaError_t (*step_pull)(const Geom&, const void* coef, const void* src, void* dst, int* flag, cudaStream_t);
     cudaError_t (*step_aa)(const Geom&, const void* coef, int odd, const void* src, void* dst, int* flag,
                            cudaStream_t);
-    // the pull step over a list of 16-cell sectors and the AA step over a fluid-cell list (boxes
-    // with walls, FP16 storage)
+    // the pull step over a list of 32-byte sectors (boxes with walls, FP16 and FP32 storage) and
+    // the AA step over a fluid-cell list (boxes with walls, FP16 storage)
     cudaError_t (*step_pull_sectors)(const Geom&, const void* coef, const CellList&, const void* src, void* dst,
                                      int* flag, cudaStream_t);
     cudaError_t (*step_aa_list)(const Geom&, const void* coef, const CellList&, int odd, const void* src, void* dst,
@@ -118,6 +118,9 @@ struct Ops {
                             cudaStream_t);
     cudaError_t (*ade_aa)(const Geom&, const void* coef, const void* u, int odd, const void* src, void* dst,
                           int* flag, cudaStream_t);
+    // the scalar pull step over the sector list (boxes with walls, FP16 and FP32 storage)
+    cudaError_t (*ade_pull_sectors)(const Geom&, const void* coef, const CellList&, const void* u, const void* src,
+                                    void* dst, int* flag, cudaStream_t);
 };
 
 // One translation unit per (lattice, storage): lbm_ops.cu compiled with LBM_Q / LBM_S, and for

@@ -302,10 +302,20 @@ struct Launch {
         return cudaGetLastError();
     }
 
+    static cudaError_t ade_pull_sectors(const Geom& g, const void* coef, const CellList& L, const void* u,
+                                        const void* src, void* dst, int* flag, cudaStream_t st) {
+        if (L.count == 0) return cudaSuccess;
+        const CF& cf = *static_cast<const CF*>(coef);
+        const unsigned long long threads = (unsigned long long)L.count * (32ull / sizeof(ST));  // a sector each
+        k_ade_pull_sectors<Q, S><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g, cf, L, vel_field(u, g),
+                                                                                   cpl(src, g), mpl(dst, g), flag);
+        return cudaGetLastError();
+    }
+
     static const Ops& ops() {
         static const Ops o = {&init,     &step_pull, &step_aa,   &step_pull_sectors, &step_aa_list, &moments,
                               &totals,   &adj_seed,  &adj_step,  &adj_init,          &link_mask,    &ade_pull,
-                              &ade_aa};
+                              &ade_aa,   &ade_pull_sectors};
         return o;
     }
 };
