@@ -172,6 +172,18 @@ int lbm_adjoint(lbm_ctx* ctx, const void* loss_grad, int n, int checkpoint_every
  * adjoint). */
 int lbm_adjoint_info(const lbm_ctx* ctx, int* sub_segment, int* prefetched);
 
+/* The recompute plan lbm_adjoint follows for one segment of `len` steps when `working` state
+ * buffers are free besides the segment start: *count sub-segment starts s_0 = 0 < ... < s_m < len
+ * are written to starts[0 .. *count - 1] (capacity entries available; *count = 1, starts = {0}, when
+ * the segment is recomputed flat, i.e. len - 1 <= working). The first recompute pass keeps the
+ * states s_1 .. s_(m-1) and every state of the last sub-segment [s_m, len); each earlier
+ * sub-segment, at most len - s_m + 1 steps, is recomputed from its start into the last one's
+ * buffers when its turn comes; the plan costs 2 len - 2 - working recompute steps (flat: len - 1).
+ * Host computation only, no context or device. Returns LBM_ERR_OOM when no such plan fits in
+ * `working` buffers, LBM_ERR_INVALID_ARG for len < 1, working < 0, a null pointer or too small a
+ * capacity. No counterpart in the paper (memory plan of the checkpointed adjoint). */
+int lbm_adjoint_plan(int len, int working, int* starts, int capacity, int* count);
+
 /* Free the adjoint's large working set (the lambda arrays and the segment states) that
  * lbm_adjoint keeps between calls; du0 and the gradients of the last call stay readable.
  * Synchronises. No counterpart in the paper (memory management of the checkpointed adjoint). */

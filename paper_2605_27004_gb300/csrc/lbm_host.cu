@@ -1324,6 +1324,16 @@ int lbm_adjoint_info(const lbm_ctx* c, int* sub_segment, int* prefetched) {
     return LBM_OK;
 }
 
+int lbm_adjoint_plan(int len, int working, int* starts, int capacity, int* count) {
+    if (len < 1 || working < 0 || !starts || !count || capacity < 1) return LBM_ERR_INVALID_ARG;
+    std::vector<int> sp;
+    if (!segment_plan(len, working, sp)) return LBM_ERR_OOM;
+    *count = (int)sp.size();
+    if ((int)sp.size() > capacity) return LBM_ERR_INVALID_ARG;
+    for (size_t j = 0; j < sp.size(); ++j) starts[j] = sp[j];
+    return LBM_OK;
+}
+
 int lbm_adjoint_release(lbm_ctx* c) {
     if (!c) return LBM_ERR_INVALID_ARG;
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));

@@ -61,6 +61,7 @@ SIGNATURES = {
     "lbm_adjoint": (_I, [_P, _P, _I, _I]),
     "lbm_adjoint_release": (_I, [_P]),
     "lbm_adjoint_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "lbm_adjoint_plan": (_I, [_I, _I, ctypes.POINTER(_I), _I, ctypes.POINTER(_I)]),
     "lbm_record_checkpoints": (_I, [_P, _I]),
     "lbm_gradients": (_I, [_P, _P, _P, _P]),
     "lbm_state_bytes": (_I, [_P, ctypes.POINTER(_S)]),
@@ -138,6 +139,20 @@ def lattice_info(q: int):
     if n != q:
         raise LBMError(n, f"unknown lattice {q}")
     return c, w
+
+
+def adjoint_plan(length: int, working: int):
+    """Sub-segment starts of the adjoint's recompute plan for a segment of `length` steps with
+    `working` free state buffers ([0] when flat), or None when no plan fits (lbm_adjoint_plan)."""
+    cap = max(1, int(length))
+    starts = (ctypes.c_int * cap)()
+    count = ctypes.c_int(0)
+    rc = load().lbm_adjoint_plan(int(length), int(working), starts, cap, ctypes.byref(count))
+    if rc == -4:
+        return None
+    if rc != 0:
+        raise LBMError(rc, f"lbm_adjoint_plan({length}, {working})")
+    return [starts[j] for j in range(count.value)]
 
 
 class _TorchAllocator:
