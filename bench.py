@@ -83,6 +83,7 @@ class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    EXTRA = ",clocks.mem,temperature.gpu,temperature.memory"  # used when this nvidia-smi accepts them
 
     def __init__(self, device_index=0):
         self.idx = device_index
@@ -91,8 +92,13 @@ class ClockSampler:
 
     def __enter__(self):
         try:
+            fields = self.FIELDS + self.EXTRA
+            probe = subprocess.run(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={fields}",
+                                    "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+            if probe.returncode != 0:
+                fields = self.FIELDS
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={fields}", "--format=csv,noheader,nounits",
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -131,7 +137,21 @@ class ClockSampler:
                     reasons.add(nm)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        extra = {"mem_mhz": [], "gpu_temp_c": [], "hbm_temp_c": []}
+        for line in self.out:  # memory clock and temperatures (N/A on some parts)
+            parts = [p.strip() for p in line.split(",")]
+            for k, key in zip(range(9, 12), extra):
+                try:
+                    extra[key].append(float(parts[k]))
+                except (ValueError, IndexError):
+                    pass
+        if extra["mem_mhz"]:
+            out["mem_mhz"] = float(np.median(extra["mem_mhz"]))
+        for key in ("gpu_temp_c", "hbm_temp_c"):
+            if extra[key]:
+                out[key + "_max"] = max(extra[key])
+        return out
 
 
 # ------------------------------------------------------------------------------------------------
